@@ -1,0 +1,563 @@
+/*
+ * mpjsvd_oracle.c -- plain CPU oracle for the mixed-precision one-sided Jacobi SVD
+ * (Gao, Ma, Shao, arXiv 2209.04626).
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
+ * leg are its only callers; the GPU library never links or calls it, and it shares no
+ * code, header or table with the GPU library.
+ *
+ * Every routine is the textbook loop nest of the algorithm it cites, in IEEE binary64
+ * (binary32 for the *_f32 routine), column-major, unblocked, single-threaded.
+ */
+#include "mpjsvd_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define AT(a, i, j, ld) ((a)[(size_t)(j) * (size_t)(ld) + (size_t)(i)])
+
+static const double U_WORK = 1.1102230246251565e-16; /* 2^-53, unit round-off of binary64 */
+static const double U_LOW = 5.9604644775390625e-08;  /* 2^-24, unit round-off of binary32 */
+
+void orc_default_params(orc_params* p)
+{
+    p->tol_alg = 1e-2;        /* Section 7.1 */
+    p->tol_orth = 1e-5;       /* Section 7.1 and the footnote of Section 3.5 */
+    p->tol_cond_coef = 1.5;   /* Section 7.1: tol_cond = 1.5 n^(1/4) */
+    p->trailing_frac = 0.25;  /* Section 3.5 footnote: check 1/4 to 1/3 of the columns */
+    p->tol = 0.0;             /* -> sqrt(n) * 2^-53 */
+    p->maxsweep = 30;
+    p->mode = 0;
+    p->precond = 0;
+}
+
+static double nrm2(int len, const double* x)
+{
+    double s = 0.0;
+    for (int i = 0; i < len; ++i) s += x[i] * x[i];
+    return sqrt(s);
+}
+
+/* ---------------------------------------------------------------------------------
+ * Householder reflector (used by the QR preconditioning of Section 3.1 and the QR of
+ * the switch, Section 3.3). H = I - tau v v^T, v[0] = 1, H x = beta e_1 with
+ * beta = -sign(x_0) |x|, the choice that avoids cancellation in x_0 - beta.
+ * ------------------------------------------------------------------------------- */
+void orc_house(int len, double* x, double* tau)
+{
+    if (len <= 1) { *tau = 0.0; return; }
+    double alpha = x[0];
+    double s = 0.0;
+    for (int i = 1; i < len; ++i) s += x[i] * x[i];
+    if (s == 0.0) { *tau = 0.0; return; } /* already a multiple of e_1: H = I */
+    double norm = sqrt(alpha * alpha + s);
+    double beta = (alpha >= 0.0) ? -norm : norm;
+    *tau = (beta - alpha) / beta;
+    double den = alpha - beta;
+    for (int i = 1; i < len; ++i) x[i] /= den; /* divide: a lone nonzero maps to +-1 exactly */
+    x[0] = beta;
+}
+
+/* Apply H = I - tau v v^T (v[0] = 1 implicit, v[1..len-1] = vtail) to column c (len). */
+static void house_apply(int len, const double* vtail, double tau, double* c)
+{
+    if (tau == 0.0) return;
+    double w = c[0];
+    for (int i = 1; i < len; ++i) w += vtail[i] * c[i];
+    w *= tau;
+    c[0] -= w;
+    for (int i = 1; i < len; ++i) c[i] -= w * vtail[i];
+}
+
+/* Plain QR, A = Q0 R1 (Alg. 4 preprocessing for m > n; Section 3.1). */
+int orc_geqrf(int m, int n, double* A, int lda, double* tau)
+{
+    if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
+    int k = m < n ? m : n;
+    for (int j = 0; j < k; ++j) {
+        double* colj = &AT(A, j, j, lda);
+        orc_house(m - j, colj, &tau[j]);
+        for (int c = j + 1; c < n; ++c) house_apply(m - j, colj, tau[j], &AT(A, j, c, lda));
+    }
+    return 0;
+}
+
+/* Businger-Golub QR with column pivoting (the RRQR of Section 3.1 / Alg. 5, step 2):
+ * at step j the remaining column of largest norm is swapped into position j, then
+ * eliminated by a Householder reflector. Column norms are downdated by the new row-j
+ * entry and recomputed from scratch when the downdate has lost more than half the
+ * digits (ratio test against the norm recorded at the last recomputation). */
+int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau)
+{
+    if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
+    const double tol3z = sqrt(U_WORK);
+    double* vn1 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* vn2 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!vn1 || !vn2) { free(vn1); free(vn2); return -9; }
+    for (int c = 0; c < n; ++c) {
+        jpvt[c] = c;
+        vn1[c] = nrm2(m, &AT(A, 0, c, lda));
+        vn2[c] = vn1[c];
+    }
+    int k = m < n ? m : n;
+    for (int j = 0; j < k; ++j) {
+        int p = j;
+        for (int c = j + 1; c < n; ++c)
+            if (vn1[c] > vn1[p]) p = c; /* first maximum wins ties */
+        if (p != j) {
+            for (int i = 0; i < m; ++i) {
+                double t = AT(A, i, j, lda);
+                AT(A, i, j, lda) = AT(A, i, p, lda);
+                AT(A, i, p, lda) = t;
+            }
+            int ti = jpvt[j]; jpvt[j] = jpvt[p]; jpvt[p] = ti;
+            vn1[p] = vn1[j];
+            vn2[p] = vn2[j];
+        }
+        double* colj = &AT(A, j, j, lda);
+        orc_house(m - j, colj, &tau[j]);
+        for (int c = j + 1; c < n; ++c) {
+            house_apply(m - j, colj, tau[j], &AT(A, j, c, lda));
+            if (vn1[c] != 0.0) {
+                double r = fabs(AT(A, j, c, lda)) / vn1[c];
+                double t = 1.0 - r * r;
+                if (t < 0.0) t = 0.0;
+                double q = vn1[c] / vn2[c];
+                if (t * q * q <= tol3z) {
+                    vn1[c] = (j + 1 < m) ? nrm2(m - j - 1, &AT(A, j + 1, c, lda)) : 0.0;
+                    vn2[c] = vn1[c];
+                } else {
+                    vn1[c] *= sqrt(t);
+                }
+            }
+        }
+    }
+    free(vn1);
+    free(vn2);
+    return 0;
+}
+
+void orc_apply_q(int trans, int m, int ncols, int k, const double* V, int ldv,
+                 const double* tau, double* C, int ldc)
+{
+    /* Q = H_0 H_1 ... H_{k-1}: Q C applies H_{k-1} first, Q^T C applies H_0 first. */
+    for (int s = 0; s < k; ++s) {
+        int j = trans ? s : (k - 1 - s);
+        const double* v = &AT(V, j, j, ldv);
+        for (int c = 0; c < ncols; ++c) house_apply(m - j, v, tau[j], &AT(C, j, c, ldc));
+    }
+}
+
+/* ---------------------------------------------------------------------------------
+ * Jacobi rotation (Section 2.1). [x_p, x_q] J with J = [c s; -s c] gives
+ *   x_p' = c x_p - s x_q,  x_q' = s x_p + c x_q,
+ * and x_p'^T x_q' = c^2 (gamma (1 - t^2) - t (beta - alpha)) with t = s / c. Setting it
+ * to zero gives t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 gamma). Of its two
+ * roots the one of modulus <= 1 gives the J closest to the identity (the footnote of
+ * Section 2.1): t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).
+ * ------------------------------------------------------------------------------- */
+double orc_rot_tangent(double alpha, double beta, double gamma)
+{
+    double zeta = (beta - alpha) / (2.0 * gamma);
+    double az = fabs(zeta);
+    double t;
+    if (az > 1e150) t = 1.0 / (2.0 * az); /* zeta^2 would overflow; t -> 1/(2|zeta|) */
+    else t = 1.0 / (az + sqrt(1.0 + az * az));
+    return (zeta >= 0.0) ? t : -t;
+}
+
+/* Alg. 1 in binary64. Cyclic order (1,2),(1,3),...,(n-1,n) of eq. (cyclic). The pair
+ * (p, q) is rotated when |x_q^T x_p| > tol |x_p| |x_q|; a sweep without rotations
+ * means convergence. alpha, beta, gamma are recomputed from the columns for each pair. */
+int orc_jacobi(int m, int n, double* X, int ldx, double* V, int ldv, int nv, double tol,
+               int maxsweep, int* sweeps, long long* rotations)
+{
+    long long rot = 0;
+    int sweep = 0, converged = 0;
+    while (sweep < maxsweep && !converged) {
+        converged = 1;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double* xp = &AT(X, 0, p, ldx);
+                double* xq = &AT(X, 0, q, ldx);
+                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    alpha += xp[i] * xp[i];
+                    beta += xq[i] * xq[i];
+                    gamma += xp[i] * xq[i];
+                }
+                if (!(fabs(gamma) > tol * sqrt(alpha) * sqrt(beta))) continue;
+                double t = orc_rot_tangent(alpha, beta, gamma);
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double s = c * t;
+                for (int i = 0; i < m; ++i) {
+                    double a = xp[i], b = xq[i];
+                    xp[i] = c * a - s * b;
+                    xq[i] = s * a + c * b;
+                }
+                if (V) {
+                    double* vp = &AT(V, 0, p, ldv);
+                    double* vq = &AT(V, 0, q, ldv);
+                    for (int i = 0; i < nv; ++i) {
+                        double a = vp[i], b = vq[i];
+                        vp[i] = c * a - s * b;
+                        vq[i] = s * a + c * b;
+                    }
+                }
+                ++rot;
+                converged = 0;
+            }
+        }
+        ++sweep;
+    }
+    if (sweeps) *sweeps = sweep;
+    if (rotations) *rotations = rot;
+    return converged ? 0 : 1;
+}
+
+/* Alg. 1 in binary32 without V (the lower-precision stage of Alg. 4). Same steps as
+ * orc_jacobi; every operation rounds to binary32. */
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int* sweeps,
+                   long long* rotations)
+{
+    long long rot = 0;
+    int sweep = 0, converged = 0;
+    while (sweep < maxsweep && !converged) {
+        converged = 1;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                float* xp = &AT(X, 0, p, ldx);
+                float* xq = &AT(X, 0, q, ldx);
+                float alpha = 0.0f, beta = 0.0f, gamma = 0.0f;
+                for (int i = 0; i < m; ++i) {
+                    alpha += xp[i] * xp[i];
+                    beta += xq[i] * xq[i];
+                    gamma += xp[i] * xq[i];
+                }
+                if (!(fabsf(gamma) > tol * sqrtf(alpha) * sqrtf(beta))) continue;
+                float zeta = (beta - alpha) / (2.0f * gamma);
+                float az = fabsf(zeta);
+                float t = (az > 1e18f) ? 1.0f / (2.0f * az) : 1.0f / (az + sqrtf(1.0f + az * az));
+                if (zeta < 0.0f) t = -t;
+                float c = 1.0f / sqrtf(1.0f + t * t);
+                float s = c * t;
+                for (int i = 0; i < m; ++i) {
+                    float a = xp[i], b = xq[i];
+                    xp[i] = c * a - s * b;
+                    xq[i] = s * a + c * b;
+                }
+                ++rot;
+                converged = 0;
+            }
+        }
+        ++sweep;
+    }
+    if (sweeps) *sweeps = sweep;
+    if (rotations) *rotations = rot;
+    return converged ? 0 : 1;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Algorithm 4.
+ * ------------------------------------------------------------------------------- */
+static int all_finite(int m, int n, const double* A, int lda)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i)
+            if (!isfinite(AT(A, i, j, lda))) return 0;
+    return 1;
+}
+
+/* max_{i != j} |y_i^T y_j| / (|y_i| |y_j|): orthogonality of Y after the switch. */
+static double scaled_offdiag(int m, int n, const double* Y)
+{
+    double worst = 0.0;
+    for (int p = 0; p < n; ++p) {
+        double np = nrm2(m, &AT(Y, 0, p, m));
+        for (int q = p + 1; q < n; ++q) {
+            double nq = nrm2(m, &AT(Y, 0, q, m));
+            double g = 0.0;
+            for (int i = 0; i < m; ++i) g += AT(Y, i, p, m) * AT(Y, i, q, m);
+            double r = (np > 0.0 && nq > 0.0) ? fabs(g) / (np * nq) : 0.0;
+            if (r > worst) worst = r;
+        }
+    }
+    return worst;
+}
+
+int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+            const orc_params* pin, orc_stats* st)
+{
+    orc_params p;
+    if (pin) p = *pin; else orc_default_params(&p);
+    orc_stats s;
+    memset(&s, 0, sizeof(s));
+    if (n < 1) { s.status = -3; if (st) *st = s; return -3; }
+    if (m < n) { s.status = -2; if (st) *st = s; return -2; }
+    if (lda < m) { s.status = -5; if (st) *st = s; return -5; }
+    if (!all_finite(m, n, A, lda)) { s.status = 2; if (st) *st = s; return 2; }
+
+    const size_t nn = (size_t)n * (size_t)n;
+    double* W0 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n); /* A, then Q0 \ R1 */
+    double* tau0 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* R = (double*)calloc(nn, sizeof(double));                      /* R1, then Q1 \ R */
+    double* tau1 = (double*)malloc(sizeof(double) * (size_t)n);
+    int* jpvt = (int*)malloc(sizeof(int) * (size_t)n);
+    double* X = (double*)calloc(nn, sizeof(double));
+    double* Y = (double*)malloc(sizeof(double) * nn);
+    double* Vacc = (double*)calloc(nn, sizeof(double));
+    double* Ux = (double*)calloc((size_t)m * (size_t)n, sizeof(double));
+    int* order = (int*)malloc(sizeof(int) * (size_t)n);
+    double* sig = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!W0 || !tau0 || !R || !tau1 || !jpvt || !X || !Y || !Vacc || !Ux || !order || !sig) {
+        s.status = -9;
+        goto done;
+    }
+
+    /* Alg. 4 preprocessing: A = Q0 R1 when m > n, else A1 = A (Q0 = I). */
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) AT(W0, i, j, m) = AT(A, i, j, lda);
+    if (m > n) {
+        orc_geqrf(m, n, W0, m, tau0);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i <= j; ++i) AT(R, i, j, n) = AT(W0, i, j, m);
+    } else {
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) AT(R, i, j, n) = AT(W0, i, j, m);
+    }
+    /* QR preconditioning: A1 P = Q1 R; X = R^T (default) or X = R (Q2 = I). */
+    orc_geqp3(n, n, R, n, jpvt, tau1);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i <= j; ++i) {
+            if (p.precond == 1) AT(X, i, j, n) = AT(R, i, j, n);
+            else AT(X, j, i, n) = AT(R, i, j, n);
+        }
+
+    /* Special cases of Section 3.5. */
+    {
+        double rnn = fabs(AT(X, n - 1, n - 1, n));
+        s.cond_r = (rnn > 0.0) ? fabs(AT(X, 0, 0, n)) / rnn : INFINITY;
+        double tol_cond = p.tol_cond_coef * pow((double)n, 0.25);
+        double maxnorm = 0.0;
+        for (int j = 0; j < n; ++j) {
+            double c = nrm2(n, &AT(X, 0, j, n));
+            if (c > maxnorm) maxnorm = c;
+        }
+        int ntrail = (int)ceil(p.trailing_frac * (double)n);
+        int trailing_small = ntrail > 0;
+        for (int j = n - ntrail; j < n; ++j)
+            if (nrm2(n, &AT(X, 0, j, n)) > sqrt(U_LOW) * maxnorm) trailing_small = 0;
+        /* orth = |Xt^T Xt - I|_max, Xt = low(X) D^-1, in binary32. */
+        float* Xt = (float*)malloc(sizeof(float) * nn);
+        if (!Xt) { s.status = -9; goto done; }
+        for (size_t i = 0; i < nn; ++i) Xt[i] = (float)X[i];
+        for (int j = 0; j < n; ++j) {
+            float d = 0.0f;
+            for (int i = 0; i < n; ++i) d += AT(Xt, i, j, n) * AT(Xt, i, j, n);
+            d = sqrtf(d);
+            if (d > 0.0f)
+                for (int i = 0; i < n; ++i) AT(Xt, i, j, n) /= d;
+        }
+        float orth = 0.0f;
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                float g = 0.0f;
+                for (int i = 0; i < n; ++i) g += AT(Xt, i, a, n) * AT(Xt, i, b, n);
+                float e = fabsf(g - (a == b ? 1.0f : 0.0f));
+                if (e > orth) orth = e;
+            }
+        free(Xt);
+        s.orth = orth;
+        if (p.mode == 2) s.branch = 4;
+        else if (p.mode == 1) s.branch = 0;
+        else if (s.cond_r <= tol_cond) s.branch = 1;
+        else if (trailing_small) s.branch = 2;
+        else if (s.orth <= p.tol_orth) s.branch = 3;
+        else s.branch = 0;
+    }
+
+    if (s.branch == 0) {
+        /* Lower-precision SVD of low(X), U only (Section 3.2). The paper would use QR-SVD
+         * when orth > tol_alg; this oracle always uses Alg. 1 (Jacobi). */
+        float* Xl = (float*)malloc(sizeof(float) * nn);
+        double* B = (double*)malloc(sizeof(double) * nn);
+        double* tau2 = (double*)malloc(sizeof(double) * (size_t)n);
+        if (!Xl || !B || !tau2) { free(Xl); free(B); free(tau2); s.status = -9; goto done; }
+        for (size_t i = 0; i < nn; ++i) Xl[i] = (float)X[i];
+        orc_jacobi_f32(n, n, Xl, n, (float)(sqrt((double)n) * U_LOW), p.maxsweep, &s.sweeps_low,
+                       &s.rot_low);
+        /* U_low = normalized columns sorted by descending norm (Alg. 1 final loop and
+         * sort), promoted to binary64. The sort matters for the switch: the QR of
+         * B = X^T U_low removes from each column its error along the directions of the
+         * columns before it, which must be those of larger singular values. */
+        float* sl = (float*)malloc(sizeof(float) * (size_t)n);
+        int* ord = (int*)malloc(sizeof(int) * (size_t)n);
+        if (!sl || !ord) { free(sl); free(ord); free(Xl); free(B); free(tau2); s.status = -9; goto done; }
+        for (int j = 0; j < n; ++j) {
+            float d = 0.0f;
+            for (int i = 0; i < n; ++i) d += AT(Xl, i, j, n) * AT(Xl, i, j, n);
+            sl[j] = sqrtf(d);
+            for (int i = 0; i < n; ++i) AT(Xl, i, j, n) = (sl[j] > 0.0f) ? AT(Xl, i, j, n) / sl[j] : 0.0f;
+            ord[j] = j;
+        }
+        for (int a = 1; a < n; ++a) { /* stable insertion sort, descending */
+            int oj = ord[a];
+            int b = a - 1;
+            while (b >= 0 && sl[ord[b]] < sl[oj]) { ord[b + 1] = ord[b]; --b; }
+            ord[b + 1] = oj;
+        }
+        /* Switch (Section 3.3, method preferred there): B = X^T double(U_low),
+         * B = Q R2, Y = X Q; the refinement's V accumulator starts at Q. */
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += AT(X, i, a, n) * (double)AT(Xl, i, ord[b], n);
+                AT(B, a, b, n) = acc;
+            }
+        free(sl);
+        free(ord);
+        orc_geqrf(n, n, B, n, tau2);
+        for (int j = 0; j < n; ++j) AT(Vacc, j, j, n) = 1.0;
+        orc_apply_q(0, n, n, n, B, n, tau2, Vacc, n); /* Vacc = Q */
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += AT(X, a, i, n) * AT(Vacc, i, b, n);
+                AT(Y, a, b, n) = acc;
+            }
+        s.switch_off = scaled_offdiag(n, n, Y);
+        free(Xl);
+        free(B);
+        free(tau2);
+    } else {
+        memcpy(Y, X, sizeof(double) * nn);
+        for (int j = 0; j < n; ++j) AT(Vacc, j, j, n) = 1.0;
+        s.switch_off = scaled_offdiag(n, n, Y);
+    }
+
+    /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated. */
+    {
+        double tol = (p.tol > 0.0) ? p.tol : sqrt((double)n) * U_WORK;
+        int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, &s.sweeps_work, &s.rot_work);
+        if (rc != 0) s.status = 1;
+    }
+
+    /* Sigma = column norms, U_X = normalized columns, sorted descending (Alg. 1). */
+    for (int j = 0; j < n; ++j) {
+        sig[j] = nrm2(n, &AT(Y, 0, j, n));
+        order[j] = j;
+    }
+    for (int a = 1; a < n; ++a) { /* stable insertion sort, descending */
+        int oj = order[a];
+        int b = a - 1;
+        while (b >= 0 && sig[order[b]] < sig[oj]) { order[b + 1] = order[b]; --b; }
+        order[b + 1] = oj;
+    }
+    /* X = U_X Sigma V_acc^T. For X = R: U_R = U_X, V_R = V_acc. For X = R^T the roles
+     * exchange: R = V_acc Sigma U_X^T, so U_R = V_acc and V_R = U_X. */
+    for (int k = 0; k < n; ++k) {
+        int j = order[k];
+        S[k] = sig[j];
+        for (int i = 0; i < n; ++i) {
+            double ux = (sig[j] > 0.0) ? AT(Y, i, j, n) / sig[j] : 0.0;
+            double uR = (p.precond == 1) ? ux : AT(Vacc, i, j, n);
+            double vR = (p.precond == 1) ? AT(Vacc, i, j, n) : ux;
+            AT(Ux, i, k, m) = uR;
+            /* V = P V_R: row jpvt[i] of V is row i of V_R (Alg. 2, V <- P V_X). */
+            AT(V, jpvt[i], k, n) = vR;
+        }
+    }
+    /* U = Q0 Q1 [U_X; 0] (Alg. 4, last line). */
+    orc_apply_q(0, n, n, n, R, n, tau1, Ux, m);
+    if (m > n) orc_apply_q(0, m, n, n, W0, m, tau0, Ux, m);
+    /* Sign convention: the largest-magnitude entry of each v_k is positive. */
+    for (int k = 0; k < n; ++k) {
+        int r = 0;
+        for (int i = 1; i < n; ++i)
+            if (fabs(AT(V, i, k, n)) > fabs(AT(V, r, k, n))) r = i;
+        double sgn = (AT(V, r, k, n) < 0.0) ? -1.0 : 1.0;
+        for (int i = 0; i < n; ++i) AT(V, i, k, n) *= sgn;
+        for (int i = 0; i < m; ++i) AT(U, i, k, m) = sgn * AT(Ux, i, k, m);
+    }
+
+done:
+    free(W0); free(tau0); free(R); free(tau1); free(jpvt); free(X); free(Y);
+    free(Vacc); free(Ux); free(order); free(sig);
+    if (st) *st = s;
+    return s.status;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Adjoint of the thin SVD A = U S V^T (m >= n, U^T U = I, V^T V = I). With
+ * dP = U^T dA V one has dS = diag(dP), U^T dU = F o (dP S + S dP^T),
+ * V^T dV = F o (S dP + dP^T S), (I - U U^T) dU = (I - U U^T) dA V S^-1, where
+ * F_ij = 1 / (s_j^2 - s_i^2) (i != j), F_ii = 0. Collecting <gS, dS> + <gU, dU> +
+ * <gV, dV> = <gA, dA> gives
+ *   gA = U [ (F o (U^T gU - gU^T U)) S + diag(gS) + S (F o (V^T gV - gV^T V)) ] V^T
+ *        + (I - U U^T) gU S^-1 V^T.
+ * ------------------------------------------------------------------------------- */
+int orc_svd_backward(int m, int n, const double* U, const double* S, const double* V,
+                     const double* gU, const double* gS, const double* gV, double* gA,
+                     double gap_tol, int* n_flagged)
+{
+    if (n < 1 || m < n) return -1;
+    const size_t nn = (size_t)n * (size_t)n;
+    double* M1 = (double*)calloc(nn, sizeof(double)); /* U^T gU */
+    double* M2 = (double*)calloc(nn, sizeof(double)); /* V^T gV */
+    double* K = (double*)calloc(nn, sizeof(double));
+    double* T = (double*)calloc((size_t)m * (size_t)n, sizeof(double));
+    if (!M1 || !M2 || !K || !T) { free(M1); free(M2); free(K); free(T); return -9; }
+    int flagged = 0;
+    for (int i = 0; i < n; ++i) {
+        if (S[i] <= U_WORK * S[0]) ++flagged;
+        for (int j = i + 1; j < n; ++j) {
+            double big = S[i] > S[j] ? S[i] : S[j];
+            if (fabs(S[i] - S[j]) <= gap_tol * big) ++flagged;
+        }
+    }
+    if (gU)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int r = 0; r < m; ++r) acc += AT(U, r, i, m) * AT(gU, r, j, m);
+                AT(M1, i, j, n) = acc;
+            }
+    if (gV)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int r = 0; r < n; ++r) acc += AT(V, r, i, n) * AT(gV, r, j, n);
+                AT(M2, i, j, n) = acc;
+            }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            if (i == j) { AT(K, i, i, n) = gS ? gS[i] : 0.0; continue; }
+            double f = 1.0 / (S[j] * S[j] - S[i] * S[i]);
+            AT(K, i, j, n) = f * (AT(M1, i, j, n) - AT(M1, j, i, n)) * S[j] +
+                             S[i] * f * (AT(M2, i, j, n) - AT(M2, j, i, n));
+        }
+    /* T = U K + (gU - U M1) S^-1 */
+    for (int j = 0; j < n; ++j)
+        for (int r = 0; r < m; ++r) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += AT(U, r, i, m) * AT(K, i, j, n);
+            if (gU) {
+                double proj = 0.0;
+                for (int i = 0; i < n; ++i) proj += AT(U, r, i, m) * AT(M1, i, j, n);
+                acc += (AT(gU, r, j, m) - proj) / S[j];
+            }
+            AT(T, r, j, m) = acc;
+        }
+    /* gA = T V^T */
+    for (int c = 0; c < n; ++c)
+        for (int r = 0; r < m; ++r) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += AT(T, r, j, m) * AT(V, c, j, n);
+            AT(gA, r, c, m) = acc;
+        }
+    free(M1); free(M2); free(K); free(T);
+    if (n_flagged) *n_flagged = flagged;
+    return 0;
+}

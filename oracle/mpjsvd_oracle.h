@@ -1,0 +1,107 @@
+/*
+ * mpjsvd_oracle.h -- plain CPU oracle for the mixed-precision one-sided Jacobi SVD
+ * (Gao, Ma, Shao, "A mixed precision Jacobi SVD algorithm", arXiv 2209.04626).
+ *
+ * TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the benchmark's
+ * CPU-baseline leg are the only callers. The GPU library neither links nor calls
+ * this code, and this code includes nothing from the GPU library.
+ *
+ * All matrices are column-major (LAPACK convention): element (i, j) of a matrix
+ * with leading dimension ld lives at a[j * ld + i]. Arithmetic is IEEE binary64
+ * unless a function name ends in _f32 (binary32 loops, used for the paper's
+ * lower-precision stage). Nothing is blocked, fused or reordered beyond what the
+ * paper's algorithms state.
+ */
+#ifndef MPJSVD_ORACLE_H
+#define MPJSVD_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Tunables of Algorithm 4 (Section 3, values used in Section 7.1). */
+typedef struct {
+    double tol_alg;        /* Jacobi vs QR-SVD choice threshold (Alg. 4), default 1e-2 */
+    double tol_orth;       /* orthogonality skip threshold (Section 3.5), default 1e-5 */
+    double tol_cond_coef;  /* tol_cond = coef * n^(1/4) (Section 7.1), default 1.5 */
+    double trailing_frac;  /* fraction of trailing columns tested (Section 3.5), default 0.25 */
+    double tol;            /* Alg. 1 threshold in working precision; <= 0 -> sqrt(n) * 2^-53 */
+    int maxsweep;          /* Alg. 1 maxiter, default 30 */
+    int mode;              /* 0 auto (Alg. 4 branch tests), 1 force the low-precision stage,
+                              2 never run it (plain FP64 preconditioned Jacobi, Alg. 2) */
+    int precond;           /* Jacobi input after the QRCP A1 P = Q1 R: 0 -> X = R^T (lower
+                              triangular; SVD of R with the roles of U and V exchanged),
+                              1 -> X = R (Alg. 4 with Q2 = I) */
+} orc_params;
+
+/* What the driver did (per call). */
+typedef struct {
+    int branch;            /* 0 low-precision stage ran; 1 skipped: cond_R small;
+                              2 skipped: trailing columns small; 3 skipped: orth <= tol_orth;
+                              4 skipped: mode 2 */
+    int sweeps_low;        /* FP32 Alg. 1 sweeps (0 if skipped) */
+    int sweeps_work;       /* FP64 Alg. 1 sweeps */
+    long long rot_low;     /* rotations applied in FP32 */
+    long long rot_work;    /* rotations applied in FP64 */
+    double cond_r;         /* |R(0,0)| / |R(n-1,n-1)| */
+    double orth;           /* max |Xt^T Xt - I| of the column-scaled low(X), FP32 */
+    double switch_off;     /* max_{i!=j} |y_i^T y_j| / (|y_i||y_j|) right after the switch */
+    int status;            /* 0 ok, 1 FP64 sweeps hit maxsweep, 2 non-finite input, <0 bad argument */
+} orc_stats;
+
+void orc_default_params(orc_params* p);
+
+/* Householder reflector (Section 3.1): overwrite x[0..len-1] (stride 1) so that
+ * x[0] = beta and x[1..] = v[1..] with v[0] = 1 implicit and H = I - tau v v^T,
+ * H * x_in = beta * e_1. */
+void orc_house(int len, double* x, double* tau);
+
+/* Plain Householder QR, A = Q R (Alg. 4, the m > n preprocessing). In place: R in
+ * the upper triangle, reflectors below it, tau[min(m,n)]. */
+int orc_geqrf(int m, int n, double* A, int lda, double* tau);
+
+/* Businger-Golub QR with column pivoting, A P = Q R (Section 3.1, Alg. 5 step 2).
+ * jpvt[i] = original index of the column in position i (0-based). Column norms are
+ * downdated after each step and recomputed when cancellation is severe. */
+int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau);
+
+/* C <- Q C (trans = 0) or Q^T C (trans = 1), Q = H_0 H_1 ... H_{k-1} from orc_geqrf /
+ * orc_geqp3 output (V, ldv, tau). C is m x ncols. */
+void orc_apply_q(int trans, int m, int ncols, int k, const double* V, int ldv,
+                 const double* tau, double* C, int ldc);
+
+/* Alg. 1 in binary64: cyclic one-sided Jacobi on X (m x n). If V != NULL, every rotation
+ * is also applied to the columns of V (nv x n). Returns 0 if converged, 1 if maxsweep
+ * sweeps ran without converging. */
+int orc_jacobi(int m, int n, double* X, int ldx, double* V, int ldv, int nv, double tol,
+               int maxsweep, int* sweeps, long long* rotations);
+
+/* Alg. 1 in binary32, no V (Alg. 4: "without generating V explicitly"). */
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int* sweeps,
+                   long long* rotations);
+
+/* Jacobi rotation for one column pair (Section 2.1): given alpha = |x_p|^2,
+ * beta = |x_q|^2, gamma = x_p^T x_q (gamma != 0), the tangent t of the rotation closest
+ * to the identity that makes [x_p, x_q] J orthogonal, J = [c s; -s c], s = c t. */
+double orc_rot_tangent(double alpha, double beta, double gamma);
+
+/* Algorithm 4 (with Algorithm 2 as its mode-2 special case): thin SVD of A (m x n,
+ * m >= n). U m x n (ldu = m), S n (descending), V n x n (ldv = n), A = U diag(S) V^T.
+ * Sign convention: each (u_i, v_i) is flipped so that the entry of v_i with the largest
+ * magnitude (lowest row index on ties) is positive. */
+int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+            const orc_params* p, orc_stats* st);
+
+/* Adjoint of the thin SVD (not in the paper; published SVD-derivative formula).
+ * Given U (m x n), S (n), V (n x n) and the cotangents gU (m x n), gS (n), gV (n x n)
+ * (each may be NULL = zero), writes gA (m x n). Pairs with
+ * |s_i - s_j| <= gap_tol * max(s_i, s_j) and singular values s_i <= 2^-53 * s_0 are
+ * counted in *n_flagged; nothing is clamped. */
+int orc_svd_backward(int m, int n, const double* U, const double* S, const double* V,
+                     const double* gU, const double* gS, const double* gV, double* gA,
+                     double gap_tol, int* n_flagged);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

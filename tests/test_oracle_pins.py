@@ -1,0 +1,330 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other than
+itself -- a closed form, an exact special case, a library routine (LAPACK through
+numpy/scipy), high-precision arithmetic (mpmath) or finite differences -- so that a
+dropped term, a wrong sign or index, or a transposed operand fails at least one test."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_04626_gb300 import inputs
+
+U64 = 2.0 ** -53
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _fro(a):
+    return float(np.linalg.norm(a))
+
+
+# ---------------------------------------------------------------- rotation (Section 2.1)
+
+def test_rotation_tangent_matches_angle_closed_form():
+    """t = tan(theta) with tan(2 theta) = 2 gamma / (alpha - beta)... in the J convention
+    x_p' = c x_p - s x_q; the minimal rotation has |theta| <= pi/4."""
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        x = rng.standard_normal((7, 2)) * rng.uniform(0.1, 10, 2)
+        a, b, g = x[:, 0] @ x[:, 0], x[:, 1] @ x[:, 1], x[:, 0] @ x[:, 1]
+        t = oracle.rot_tangent(a, b, g)
+        # J = [c s; -s c]: x_p'^T x_q' = 0  <=>  tan(2 theta) = 2 g / (b - a) with t = tan(theta)
+        theta = 0.5 * np.arctan2(2 * g, b - a)
+        if theta > np.pi / 4:
+            theta -= np.pi / 2
+        if theta < -np.pi / 4:
+            theta += np.pi / 2
+        assert abs(t) <= 1.0
+        assert t == pytest.approx(np.tan(theta), rel=1e-12, abs=1e-15)
+        c = 1 / np.sqrt(1 + t * t)
+        s = c * t
+        xp = c * x[:, 0] - s * x[:, 1]
+        xq = s * x[:, 0] + c * x[:, 1]
+        assert abs(xp @ xq) <= 8 * U64 * np.linalg.norm(xp) * np.linalg.norm(xq) * 7
+        # alpha' = alpha - t gamma, beta' = beta + t gamma
+        assert xp @ xp == pytest.approx(a - t * g, rel=1e-13)
+        assert xq @ xq == pytest.approx(b + t * g, rel=1e-13)
+
+
+def test_golden_2x2():
+    """Worked example in tests/golden/svd_2x2.txt (closed form of Section 2.1)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "svd_2x2.txt"))
+            if l.strip() and not l.startswith("#")]
+    vals = [r for r in rows if all(_isnum(t) for t in r)]
+    A = np.array([float(v) for v in vals[0]]).reshape(2, 2)
+    s1sq, s2sq = (float(v) for v in vals[1])
+    t_expect = float(vals[2][0])
+    x1, x2 = A[:, 0], A[:, 1]
+    assert oracle.rot_tangent(x1 @ x1, x2 @ x2, x1 @ x2) == t_expect
+    U, S, V, st = oracle.svd(A, mode="plain")
+    assert S[0] ** 2 == pytest.approx(s1sq, rel=4 * U64)
+    assert S[1] ** 2 == pytest.approx(s2sq, rel=8 * U64)
+    assert np.allclose(np.abs(V), np.full((2, 2), np.sqrt(0.5)), atol=4 * U64)
+
+
+def _isnum(t):
+    try:
+        float(t)
+        return True
+    except ValueError:
+        return False
+
+
+def test_2x2_closed_form_singular_values():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        A = rng.standard_normal((2, 2))
+        _, S, _, _ = oracle.svd(A, mode="plain")
+        a, b, g = A[:, 0] @ A[:, 0], A[:, 1] @ A[:, 1], A[:, 0] @ A[:, 1]
+        r = np.sqrt(((a - b) / 2) ** 2 + g * g)
+        s_closed = np.sqrt([(a + b) / 2 + r, (a + b) / 2 - r])
+        assert S[0] == pytest.approx(s_closed[0], rel=1e-14)
+        assert S[0] * S[1] == pytest.approx(abs(np.linalg.det(A)), rel=1e-13)
+        assert S @ S == pytest.approx(_fro(A) ** 2, rel=1e-14)
+
+
+# ---------------------------------------------------------------- exact special cases
+
+@pytest.mark.parametrize("mode", ["plain", "mixed", "auto"])
+def test_diagonal_input_exact(mode):
+    rng = np.random.default_rng(2)
+    d = rng.permutation(np.logspace(0, -9, 12)) * rng.choice([-1.0, 1.0], 12)
+    A = np.diag(d)
+    U, S, V, st = oracle.svd(A, mode=mode)
+    assert np.array_equal(S, np.sort(np.abs(d))[::-1])
+    assert st["rot_work"] == 0
+    # U, V are signed permutations with U diag(S) V^T = A exactly
+    assert np.array_equal(np.abs(V), np.abs(V).round())
+    assert np.array_equal((U * S) @ V.T, A)
+
+
+def test_permuted_diagonal_rectangular_exact():
+    rng = np.random.default_rng(3)
+    m, n = 9, 6
+    d = rng.uniform(0.5, 3.0, n) * rng.choice([-1.0, 1.0], n)
+    D = np.zeros((m, n))
+    D[:n, :n] = np.diag(d)
+    A = D[rng.permutation(m)][:, rng.permutation(n)]
+    U, S, V, st = oracle.svd(A, mode="plain")
+    assert np.array_equal(S, np.sort(np.abs(d))[::-1])
+    assert np.allclose((U * S) @ V.T, A, atol=0, rtol=0) or np.abs((U * S) @ V.T - A).max() < 4 * U64 * 3
+
+
+# ---------------------------------------------------------------- known sigma, invariants
+
+@pytest.mark.parametrize("mode", ["plain", "mixed", "auto"])
+def test_known_sigma_and_invariants(mode):
+    rng = np.random.default_rng(7)
+    m, n = 80, 48
+    sigma = np.logspace(0, -6, n)
+    A = inputs.known_sigma(rng, m, n, sigma)
+    U, S, V, st = oracle.svd(A, mode=mode)
+    assert st["status"] == 0
+    # the stored A is sigma's matrix up to rounding: compare against LAPACK on the same A
+    s_lapack = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(S - s_lapack) / s_lapack) < 1e-9  # LAPACK gesdd is not relatively accurate
+    assert np.max(np.abs(S - sigma) / sigma) < 1e-8
+    assert S @ S == pytest.approx(_fro(A) ** 2, rel=n * U64 * 4)
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 64 * n * U64
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 64 * n * U64
+    assert _fro(A - (U * S) @ V.T) / _fro(A) <= 1e-13
+    colerr = np.linalg.norm(A - (U * S) @ V.T, axis=0) / np.linalg.norm(A, axis=0)
+    assert colerr.max() <= 1e-13
+    assert np.all(np.diff(S) <= 0)
+
+
+def test_matches_lapack_well_conditioned():
+    """Well-conditioned input: every accurate SVD agrees to ~u; LAPACK (numpy) pins sigma
+    and the singular subspaces."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((60, 40))
+    U, S, V, _ = oracle.svd(A)
+    Ul, Sl, Vlt = np.linalg.svd(A, full_matrices=False)
+    assert np.max(np.abs(S - Sl) / Sl) < 1e-13
+    # singular vectors agree up to sign (simple, well separated singular values)
+    sgn = np.sign(np.sum(V * Vlt.T, axis=0))
+    assert np.abs(V - Vlt.T * sgn).max() < 1e-11
+    assert np.abs(U - Ul * sgn).max() < 1e-11
+
+
+def test_high_precision_reference_tiny():
+    """mpmath at 40 digits as an independent reference on a graded 6 x 4 matrix."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((6, 4)) * np.array([1.0, 1e-3, 1e-6, 1e-9])
+    _, S, _, _ = oracle.svd(A, mode="plain")
+    M = mpmath.matrix(A.tolist())
+    s_hp = mpmath.svd_r(M, compute_uv=False)
+    s_hp = sorted([float(x) for x in s_hp], reverse=True)
+    assert np.max(np.abs(S - s_hp) / np.array(s_hp)) < 1e-14
+
+
+def test_scaling_invariance_columns_exact():
+    """Scaling a column by a power of two scales nothing but that column's data: the
+    oracle's sigma of A D (D = powers of two) equals that of the un-graded matrix only
+    through the SVD -- so compare against the permutation-invariance instead: permuting
+    the columns of A leaves sigma unchanged (the QRCP pivots see the same norms)."""
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((30, 20))
+    _, S1, _, _ = oracle.svd(A)
+    _, S2, _, _ = oracle.svd(A[:, rng.permutation(20)])
+    assert np.max(np.abs(S1 - S2) / S1) < 1e-13
+
+
+# ---------------------------------------------------------------- QR and QRCP
+
+def test_geqrf_matches_lapack():
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((50, 30))
+    QR, tau = oracle.geqrf(A)
+    R = np.triu(QR[:30])
+    R_lapack = np.linalg.qr(A, mode="r")
+    assert np.abs(R - R_lapack).max() < 1e-13 * np.abs(R).max()
+    Q = oracle.apply_q(QR, tau, np.eye(50)[:, :30])
+    assert np.abs(Q.T @ Q - np.eye(30)).max() < 30 * U64 * 8
+    assert np.abs(Q @ R - A).max() < 1e-14 * 50
+    # Q^T applied after Q gives back the identity columns
+    back = oracle.apply_q(QR, tau, Q, trans=True)
+    assert np.abs(back - np.eye(50)[:, :30]).max() < 1e-14
+
+
+def test_geqp3_matches_lapack_pivots():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((40, 25)) * np.logspace(0, -4, 25)[rng.permutation(25)]
+    QR, jpvt, tau = oracle.geqp3(A)
+    R = np.triu(QR[:25])
+    Rl, piv = scipy_linalg.qr(A, mode="r", pivoting=True)
+    assert np.array_equal(jpvt, piv)
+    assert np.abs(R - Rl[:25]).max() < 1e-12 * np.abs(R).max()
+    assert np.all(np.abs(np.diag(R))[:-1] >= np.abs(np.diag(R))[1:])
+    Q = oracle.apply_q(QR, tau, np.eye(40)[:, :25])
+    err = np.linalg.norm(Q @ R - A[:, jpvt], axis=0) / np.linalg.norm(A[:, jpvt], axis=0)
+    assert err.max() < 25 * U64 * 16
+
+
+# ---------------------------------------------------------------- Alg. 1 in both precisions
+
+def test_jacobi_f64_and_f32_converge_to_svd():
+    rng = np.random.default_rng(14)
+    n = 24
+    X = inputs.known_sigma(rng, n, n, np.logspace(0, -3, n))
+    Xi, V, sw, rot, rc = oracle.jacobi(X, np.eye(n))
+    assert rc == 0
+    S = np.linalg.norm(Xi, axis=0)
+    Sl = np.linalg.svd(X, compute_uv=False)
+    assert np.max(np.abs(np.sort(S)[::-1] - Sl) / Sl) < 1e-12
+    assert np.abs(V.T @ V - np.eye(n)).max() < 64 * n * U64
+    assert np.abs(X @ V - Xi).max() < 1e-13  # X V = X_inf: V accumulated every rotation
+    Xf, swf, rotf, rcf = oracle.jacobi_f32(X)
+    assert rcf == 0
+    Sf = np.sort(np.linalg.norm(Xf.astype(np.float64), axis=0))[::-1]
+    assert np.max(np.abs(Sf - Sl) / Sl) < 2e-4  # u_low * kappa(B_c) scale
+    Xn = Xf.astype(np.float64) / np.linalg.norm(Xf.astype(np.float64), axis=0)
+    assert np.abs(Xn.T @ Xn - np.eye(n)).max() < 1e-5
+
+
+def test_mixed_and_plain_agree():
+    rng = np.random.default_rng(15)
+    A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
+    Um, Sm, Vm, stm = oracle.svd(A, mode="mixed")
+    Up, Sp, Vp, stp = oracle.svd(A, mode="plain")
+    assert stm["branch"] == 0 and stp["branch"] == 4
+    assert np.max(np.abs(Sm - Sp) / Sp) < 1e-13
+    assert np.abs(Vm - Vp).max() < 1e-9  # gaps >= 17% -> vectors well determined
+    assert stm["sweeps_work"] <= 4 < stp["sweeps_work"]  # "typically three sweeps" (Section 3.4)
+    assert stm["switch_off"] < 1e-4  # orthogonal to O(u_low) after the switch (Section 4)
+
+
+# ---------------------------------------------------------------- branch tests (Section 3.5)
+
+def test_branch_cond_small():
+    rng = np.random.default_rng(16)
+    A = inputs.orthonormal(rng, 40, 32) * 3.0  # kappa(R) = 1
+    _, _, _, st = oracle.svd(A)
+    assert st["branch_name"] == "skip_cond"
+
+
+def test_branch_trailing_small():
+    rng = np.random.default_rng(17)
+    n = 40
+    d = np.ones(n)
+    d[-n // 3:] = 1e-7
+    A = rng.standard_normal((n, n)) * d
+    _, _, _, st = oracle.svd(A)
+    assert st["branch_name"] == "skip_trailing"
+
+
+def test_branch_orth():
+    rng = np.random.default_rng(18)
+    n = 40
+    A = inputs.orthonormal(rng, n, n) * np.logspace(0, -3, n)  # orthogonal, graded columns
+    _, _, _, st = oracle.svd(A)
+    assert st["branch_name"] == "skip_orth"
+    assert st["orth"] <= 1e-5
+
+
+def test_branch_runs_low_precision():
+    rng = np.random.default_rng(24)
+    A = inputs.known_sigma(rng, 64, 32, np.logspace(0, -2, 32))
+    _, _, _, st = oracle.svd(A)
+    assert st["branch_name"] == "mixed"
+
+
+def test_precond_r_and_rt_agree():
+    """X = R (Q2 = I) and X = R^T give the same SVD (roles of U and V exchanged)."""
+    rng = np.random.default_rng(25)
+    A = inputs.known_sigma(rng, 70, 40, np.logspace(0, -4, 40))
+    U1, S1, V1, st1 = oracle.svd(A, mode="mixed", precond="rt")
+    U2, S2, V2, st2 = oracle.svd(A, mode="mixed", precond="r")
+    assert np.max(np.abs(S1 - S2) / S2) < 1e-13
+    assert np.abs(U1 - U2).max() < 1e-9 and np.abs(V1 - V2).max() < 1e-9
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _loss(A, w, GU, GV):
+    U, S, V, _ = oracle.svd(A, mode="plain")
+    return w @ S + np.sum(GU * U) + np.sum(GV * V)
+
+
+def test_adjoint_sigma_only_closed_form():
+    """d sigma_i / dA = u_i v_i^T, so for L = sum w_i sigma_i, gA = U diag(w) V^T."""
+    rng = np.random.default_rng(19)
+    A = inputs.known_sigma(rng, 12, 7, np.logspace(0, -1, 7))
+    U, S, V, _ = oracle.svd(A)
+    w = rng.standard_normal(7)
+    gA, nf = oracle.svd_backward(U, S, V, gS=w)
+    assert np.abs(gA - (U * w) @ V.T).max() < 1e-14
+    assert nf == 0
+
+
+@pytest.mark.parametrize("shape", [(9, 5), (6, 6)])
+def test_adjoint_central_differences(shape):
+    rng = np.random.default_rng(20 + shape[0])
+    m, n = shape
+    A = inputs.known_sigma(rng, m, n, np.logspace(0, -1, n))
+    U, S, V, _ = oracle.svd(A, mode="plain")
+    w = rng.standard_normal(n)
+    GU = rng.standard_normal((m, n))
+    GV = rng.standard_normal((n, n))
+    gA, nf = oracle.svd_backward(U, S, V, GU, w, GV)
+    h = 1e-6
+    fd = np.zeros_like(A)
+    for i in range(m):
+        for j in range(n):
+            E = np.zeros_like(A)
+            E[i, j] = h
+            fd[i, j] = (_loss(A + E, w, GU, GV) - _loss(A - E, w, GU, GV)) / (2 * h)
+    assert np.abs(fd - gA).max() < 1e-6 * max(1.0, np.abs(gA).max())
+    assert nf == 0
+
+
+def test_adjoint_flags_near_degenerate():
+    rng = np.random.default_rng(23)
+    s = np.array([1.0, 0.5, 0.5 * (1 + 1e-9), 0.1])
+    A = inputs.known_sigma(rng, 6, 4, s)
+    U, S, V, _ = oracle.svd(A)
+    _, nf = oracle.svd_backward(U, S, V, gS=np.ones(4), gap_tol=1e-6)
+    assert nf == 1
