@@ -1,0 +1,384 @@
+"""Benchmark: SVDs/s of the mixed-precision Jacobi SVD on one GB300 (per rank), next to the
+plain FP64 Jacobi on the same GPU and the CPU oracle.
+
+Workload (one step = one full SVD, every stage of the hot path): the single 2048 x 1024
+FP64 matrix A = B D, B with singular values log-spaced 1 .. 1e-3 (Haar factors), D =
+diag(10^U(-8, 0)), seed 1. The mixed path is forced (the paper's low-precision stage
+runs); the plain path and the automatic branch choice are timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Timing: CUDA events on the library's stream around each
+step, L2 flushed (256 MiB write) before every timed step, max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
+WORKLOAD = ("precision_2048x1024: A = B D, B = W1 diag(logspace(0,-3,1024)) W2^T (Haar), "
+            "D = diag(10^U(-8,0)), seed 1, FP64 column-major")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=2048)
+    p.add_argument("--n", type=int, default=1024)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--plain-steps", type=int, default=3)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ oracle
+
+def oracle_sample(A, sweeps_low, sweeps_work):
+    """Time the CPU oracle's stages on the same matrix: the QR preconditioning (plain QR,
+    then QRCP of R1), one binary32 sweep on low(X) and one binary64 sweep with V on X,
+    and extrapolate the SVD time with the sweep counts. The switch and the assembly of U
+    are not timed (so the estimate is a lower bound of the oracle's time)."""
+    import oracle
+    n = A.shape[1]
+    t0 = time.perf_counter()
+    QR, tau = oracle.geqrf(A)
+    R1 = np.triu(QR[:n])
+    QR2, jpvt, tau2 = oracle.geqp3(R1)
+    t_pre = time.perf_counter() - t0
+    X = np.asfortranarray(np.triu(QR2[:n]).T)
+    t0 = time.perf_counter()
+    oracle.jacobi_f32(X.astype(np.float32), maxsweep=1)
+    t32 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.jacobi(X, np.eye(n), maxsweep=1)
+    t64 = time.perf_counter() - t0
+    est = t_pre + sweeps_low * t32 + sweeps_work * t64
+    return {"sample_s": t_pre + t32 + t64, "est_svd_s": est, "t_precond": t_pre,
+            "t_sweep32": t32, "t_sweep64": t64}
+
+
+def cpu_baseline_obj(res, sweeps_low, sweeps_work, m, n):
+    return {"value": 1.0 / res["est_svd_s"], "unit": "SVDs/s", "cores": 1, "kind": "oracle",
+            "sample": ("single-threaded C oracle on the %dx%d input: QR + QRCP (%.1f s), one "
+                       "binary32 sweep (%.1f s), one binary64 sweep with V (%.1f s); SVD time "
+                       "extrapolated with %d + %d sweeps (switch and U assembly not counted)"
+                       % (m, n, res["t_precond"], res["t_sweep32"], res["t_sweep64"],
+                          sweeps_low, sweeps_work))}
+
+
+# ------------------------------------------------------------------------------ dist
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    from paper_2209_04626_gb300 import inputs
+    import oracle
+    oracle.lib()
+    A = inputs.precision_2048x1024(m=args.m, n=args.n)
+    sweeps_low, sweeps_work = 8, 4  # typical counts of the mixed path on this input
+    for _ in range(args.warmup):
+        oracle_sample(A, sweeps_low, sweeps_work)
+    ests, samples = [], []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle_sample(A, sweeps_low, sweeps_work)
+        ests.append(r["est_svd_s"])
+        samples.append(r)
+    wall = time.perf_counter() - t_all
+    v = len(ests) / sum(ests)
+    cb = cpu_baseline_obj(samples[-1], sweeps_low, sweeps_work, args.m, args.n)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "SVDs/s", "value": v, "unit": "SVDs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(ests) / len(ests), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "mode": "mixed",
+                       "parallelism": "replicas"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "SVDs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------ ours
+
+def flops_sweeps(n, sweeps, rotations):
+    """Algorithmic FP64 flops of the refinement sweeps: a dot product (2n) for every pair
+    of every sweep, plus the scaled rotation of the pair's rows of Y and V (4n + 4n) for
+    every rotation applied."""
+    return sweeps * n * (n - 1) / 2 * 2 * n + rotations * 8 * n
+
+
+def flops_svd_fp64(m, n, sweeps_work):
+    """Algorithmic FP64 flops of the whole mixed SVD (QRCP, switch, refinement, U)."""
+    qrcp = 2 * m * n * n - 2 * n ** 3 / 3
+    switch = n ** 3 + 4 * n ** 3 / 3 + 4 * n ** 3 / 3 + n ** 3   # tri GEMM, QR, form Q, tri GEMM
+    sweeps = sweeps_work * n * (n - 1) / 2 * (2 * n + 8 * n)
+    final = 4 * m * n * n - 2 * n ** 3
+    return qrcp + switch + sweeps + final
+
+
+def ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2209_04626_gb300 import inputs, mpjsvd
+    m, n = args.m, args.n
+    A_np = inputs.precision_2048x1024(m=m, n=n)
+    A = mpjsvd.colmajor(torch.from_numpy(A_np), dev)
+    U = mpjsvd.empty_colmajor(m, n, dev)
+    S = torch.empty(n, dtype=torch.float64, device=dev)
+    V = mpjsvd.empty_colmajor(n, n, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    h = mpjsvd.Handle(mode="mixed", timing=1)
+
+    def one(handle):
+        handle.svd(A, out=(U, S, V))
+
+    # warm-up
+    for _ in range(args.warmup):
+        one(h)
+    torch.cuda.synchronize()
+    st0 = h.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    per_step_stats = []
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        one(h)
+        ev[k][1].record(stream)
+        per_step_stats.append(h.stats())  # synchronizes; outside the event pair
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    st = per_step_stats[-1]
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel: the FP64 refinement sweeps
+    work_ms = [s["ms_work"] for s in per_step_stats]
+    avg_work_ms = sum(work_ms) / len(work_ms)
+    fl_sweeps = statistics.mean(flops_sweeps(n, s["sweeps_work"], s["rot_work"]) for s in per_step_stats)
+    achieved = fl_sweeps / (avg_work_ms / 1000.0) / 1e12
+    phases = {k: statistics.mean(s[k] for s in per_step_stats)
+              for k in ["ms_qr", "ms_branch", "ms_low", "ms_switch", "ms_work", "ms_final"]}
+
+    # accuracy of the timed outputs (torch FP64 matmuls, verification only)
+    with torch.no_grad():
+        R = A - (U * S) @ V.t()
+        bw = float(torch.linalg.norm(R) / torch.linalg.norm(A))
+        eye = torch.eye(n, dtype=torch.float64, device=dev)
+        orthU = float((U.t() @ U - eye).abs().max())
+        orthV = float((V.t() @ V - eye).abs().max())
+    S_mixed = S.clone()
+
+    # plain FP64 Jacobi on the same GPU and the automatic branch choice
+    hp = mpjsvd.Handle(mode="plain", timing=1)
+    Up, Sp, Vp = U.clone(), S.clone(), V.clone()
+    hp.svd(A, out=(Up, Sp, Vp))
+    torch.cuda.synchronize()
+    pms = []
+    for k in range(args.plain_steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hp.svd(A, out=(Up, Sp, Vp))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms.append(e0.elapsed_time(e1))
+    stp = hp.stats()
+    sig_rel_mixed_vs_plain = float(((S_mixed - Sp).abs() / Sp).max())
+    ha = mpjsvd.Handle(mode="auto")
+    ha.svd(A, out=(Up, Sp, Vp))
+    sta = ha.stats()
+
+    # end to end through the public API: pinned host A -> device, SVD, U, S, V -> host
+    A_host = torch.from_numpy(np.asfortranarray(A_np).T.copy()).t().pin_memory()
+    U_host = torch.empty((n, m), dtype=torch.float64).t().pin_memory()
+    S_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    V_host = torch.empty((n, n), dtype=torch.float64).t().pin_memory()
+    A_dev = mpjsvd.empty_colmajor(m, n, dev)
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A_dev.copy_(A_host, non_blocking=True)
+        h.svd(A_dev, out=(U, S, V))
+        U_host.copy_(U, non_blocking=True)
+        S_host.copy_(S, non_blocking=True)
+        V_host.copy_(V, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = oracle_sample(A_np, st["sweeps_low"], st["sweeps_work"])
+            cpu = cpu_baseline_obj(res, st["sweeps_low"], st["sweeps_work"], m, n)
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
+                   "sample": "failed: %s" % ex}
+
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "sweep_fp64_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("m") == m and tj.get("n") == n:
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": "SVDs/s", "value": value, "unit": "SVDs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "mode": "mixed",
+                       "parallelism": "replicas", "l2": "flushed (256 MiB write) before each step",
+                       "block_w_low": st["block_w_low"], "block_w_work": st["block_w_work"]},
+            "roofline": {"kernel": "k_sweeps<double> (FP64 refinement sweeps)", "bound": "alu",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                         "flops_per_launch": fl_sweeps, "ms_per_launch": avg_work_ms},
+            "phases_ms": phases,
+            "sweeps": {"low": st["sweeps_low"], "work": st["sweeps_work"],
+                       "rot_low": st["rot_low"], "rot_work": st["rot_work"]},
+            "fp64_gflops_whole_svd": flops_svd_fp64(m, n, st["sweeps_work"]) / (total_ms / args.steps) / 1e6,
+            "compare": {"plain_svds_per_s": 1000.0 / statistics.mean(pms),
+                        "plain_ms": statistics.mean(pms), "plain_sweeps_work": stp["sweeps_work"],
+                        "mixed_over_plain": statistics.mean(pms) / (total_ms / args.steps),
+                        "auto_branch": sta["branch_name"],
+                        "max_rel_sigma_mixed_vs_plain": sig_rel_mixed_vs_plain},
+            "accuracy": {"backward_fro": bw, "orth_U_max": orthU, "orth_V_max": orthV,
+                         "bound_orth": 64 * n * 2.0 ** -53, "status": st["status"]},
+            "e2e": {"value": e2e_value, "unit": "SVDs/s", "h2d_bytes_per_step": m * n * 8,
+                    "d2h_bytes_per_step": (m * n + n + n * n) * 8},
+            "gpu_launches": int(sum(s["launches"] for s in per_step_stats)),
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        print(json.dumps(line))
+    h.close()
+    hp.close()
+    ha.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

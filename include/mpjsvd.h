@@ -1,0 +1,160 @@
+/*
+ * mpjsvd.h -- C ABI of libmpjsvd, a GB300 (sm_103a) implementation of the mixed-precision
+ * one-sided Jacobi SVD of Gao, Ma and Shao ("A mixed precision Jacobi SVD algorithm",
+ * arXiv 2209.04626).
+ *
+ * What is computed: the thin SVD A = U diag(S) V^T of a dense real m x n matrix
+ * (m >= n), to high relative accuracy, by Algorithm 4 of the paper:
+ *   1. QR preconditioning (Section 3.1): Householder QR with column pivoting of A
+ *      (optionally preceded by a plain QR when m > n), A P = Q R;
+ *   2. the special-case tests of Section 3.5 (cond_R, small trailing columns, orth);
+ *   3. a binary32 one-sided Jacobi SVD (Alg. 1, Section 3.2) of the triangular factor,
+ *      left singular vectors only;
+ *   4. the precision switch of Section 3.3: B = X^T U_low, B = Q R2, Y = X Q;
+ *   5. binary64 one-sided Jacobi refinement of Y (Alg. 1, Section 3.4) accumulating V;
+ *   6. Sigma = column norms, U_X = normalized columns, sorted descending; U and V are
+ *      assembled from the factors (Alg. 4, last line).
+ * Every stage runs as hand-written CUDA kernels on the handle's stream.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major FP64 (element (i, j) at ptr[j * ld + i]).
+ *   - Matrix pointers are DEVICE pointers owned by the caller; the library never frees
+ *     them and never modifies the input A. Outputs are fully overwritten.
+ *   - Calls are asynchronous and stream-ordered on the handle's stream: a return value of
+ *     0 means "arguments valid, work enqueued". Numeric status (non-convergence,
+ *     non-finite input, a device wait that timed out) is read with mpjsvd_get_stats(),
+ *     which synchronizes the stream.
+ *   - Return values: 0 = success; -i = argument i (1-based, the handle counts as 1) is
+ *     invalid; MPJSVD_ERR_CUDA (-100) = a CUDA call failed (see mpjsvd_last_error());
+ *     MPJSVD_ERR_NOMEM (-101) = the workspace could not be allocated.
+ *   - The handle owns a device workspace that grows on demand (cudaMalloc) and is freed
+ *     by mpjsvd_destroy(). A handle must not be used from two host threads at once.
+ */
+#ifndef MPJSVD_H
+#define MPJSVD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPJSVD_ERR_CUDA (-100)
+#define MPJSVD_ERR_NOMEM (-101)
+
+/* Numeric status bits (mpjsvd_stats.status, batched info[]). */
+#define MPJSVD_STATUS_OK 0
+#define MPJSVD_STATUS_NOT_CONVERGED 1  /* a Jacobi stage hit maxsweep sweeps */
+#define MPJSVD_STATUS_NONFINITE 2      /* A contains Inf or NaN; outputs are not meaningful */
+#define MPJSVD_STATUS_TIMEOUT 4        /* a bounded device wait gave up; outputs not meaningful */
+#define MPJSVD_STATUS_ZERO_SIGMA 8     /* some singular value is exactly zero (rank deficient) */
+
+/* Algorithm choices. */
+#define MPJSVD_MODE_AUTO 0   /* Alg. 4 special-case tests decide whether stage 3 runs */
+#define MPJSVD_MODE_MIXED 1  /* always run the binary32 stage (force the mixed path) */
+#define MPJSVD_MODE_PLAIN 2  /* never run it: plain FP64 preconditioned Jacobi (Alg. 2) */
+
+#define MPJSVD_PRECOND_RT 0  /* Jacobi on X = R^T (lower triangular); default */
+#define MPJSVD_PRECOND_R 1   /* Jacobi on X = R (Alg. 4 with Q2 = I) */
+
+typedef struct mpjsvd_ctx* mpjsvd_handle;
+
+/* Tunables. Defaults (mpjsvd_default_params) are the paper's values of Section 7.1. */
+typedef struct {
+    double tol_alg;       /* 1e-2: recorded only (the binary32 stage always uses Jacobi) */
+    double tol_orth;      /* 1e-5: skip stage 3 when |Xt^T Xt - I|_max <= tol_orth (Sec. 3.5) */
+    double tol_cond_coef; /* 1.5: skip stage 3 when |R11|/|Rnn| <= coef * n^(1/4) (Sec. 3.5) */
+    double trailing_frac; /* 0.25: skip stage 3 when the last ceil(frac*n) columns of X all
+                             have norm <= 2^-12 * max column norm (Sec. 3.5 footnote) */
+    int maxsweep;         /* 30: Alg. 1 maxiter, both precisions */
+    int block_w;          /* column-block width of the sweeps; 0 = pick from the size */
+    int mode;             /* MPJSVD_MODE_* */
+    int precond;          /* MPJSVD_PRECOND_* */
+    int qr_first;         /* 1: plain QR of A before the QRCP when m > n (Alg. 4 lines 1-3);
+                             0 (default): QRCP applied to A directly (same R and P) */
+    int timing;           /* 1: record per-phase CUDA-event times in mpjsvd_stats */
+} mpjsvd_params;
+
+/* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
+typedef struct {
+    int status;           /* MPJSVD_STATUS_* bits */
+    int branch;           /* 0 stage 3 ran; 1 skipped: cond_R; 2 skipped: trailing columns;
+                             3 skipped: orth; 4 skipped: MPJSVD_MODE_PLAIN */
+    int sweeps_low;       /* binary32 sweeps (0 if skipped) */
+    int sweeps_work;      /* binary64 sweeps */
+    long long rot_low;    /* rotations applied in binary32 */
+    long long rot_work;   /* rotations applied in binary64 */
+    double cond_r;        /* |R(0,0)| / |R(n-1,n-1)| */
+    double orth;          /* |Xt^T Xt - I|_max (computed in MPJSVD_MODE_AUTO only, else -1) */
+    int block_w_low;      /* block widths used */
+    int block_w_work;
+    float ms_qr;          /* per-phase times (ms) when params.timing = 1, else 0 */
+    float ms_branch;
+    float ms_low;
+    float ms_switch;
+    float ms_work;
+    float ms_final;
+    int launches;         /* CUDA kernels the call launched (gated-off stages included) */
+} mpjsvd_stats;
+
+/* Fill *p with the defaults. Returns 0, or -1 if p is NULL. */
+int mpjsvd_default_params(mpjsvd_params* p);
+
+/* Create a handle on the current CUDA device. p may be NULL (defaults). cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream); it can be changed with
+ * mpjsvd_set_stream(). */
+int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream);
+
+int mpjsvd_set_stream(mpjsvd_handle h, void* cuda_stream);
+int mpjsvd_set_params(mpjsvd_handle h, const mpjsvd_params* p);
+
+/* Thin SVD of one matrix (Algorithm 4).
+ *   m, n : 1 <= n <= m <= 24576, n <= 12288
+ *   A    : device, m x n, leading dimension lda >= m; not modified
+ *   U    : device, m x n output, leading dimension m
+ *   S    : device, n output, descending
+ *   V    : device, n x n output, leading dimension n
+ *   tol  : Alg. 1 threshold of the binary64 stage; <= 0 selects sqrt(n) * 2^-53
+ * A = U diag(S) V^T with U^T U = I, V^T V = I. Sign convention: each pair (u_k, v_k) is
+ * flipped so that the entry of v_k with the largest magnitude is positive (ties: lowest
+ * row index). */
+int mpjsvd_svd(mpjsvd_handle h, int m, int n, const double* A, int lda, double* U, double* S,
+               double* V, double tol);
+
+/* Thin SVDs of `batch` independent matrices of uneven sizes in one persistent launch
+ * (one CTA per matrix, largest first).
+ *   m, n, lda : HOST arrays of length batch (1 <= n_i <= m_i <= 1024, n_i <= 512,
+ *               lda_i >= m_i)
+ *   A, U, S, V: DEVICE arrays of length batch holding device pointers laid out as in
+ *               mpjsvd_svd (U_i leading dimension m_i, V_i leading dimension n_i)
+ *   info      : DEVICE int array of length batch, written with the MPJSVD_STATUS_* bits
+ *               of each matrix
+ * Same algorithm, parameters and sign convention as mpjsvd_svd. */
+int mpjsvd_svd_batched(mpjsvd_handle h, int batch, const int* m, const int* n, const int* lda,
+                       const double* const* A, double* const* U, double* const* S,
+                       double* const* V, double tol, int* info);
+
+/* Adjoint of the thin SVD (not part of the paper). Given U (m x n), S (n, descending,
+ * positive), V (n x n) from mpjsvd_svd and the cotangents gU (m x n), gS (n), gV (n x n)
+ * (device; each may be NULL = zero), writes
+ *   gA = U [(F o (U^T gU - gU^T U)) S + diag(gS) + S (F o (V^T gV - gV^T V))] V^T
+ *        + (I - U U^T) gU S^-1 V^T,     F_ij = 1/(s_j^2 - s_i^2) (i != j), F_ii = 0,
+ * (device, m x n, leading dimension m). Near-degenerate inputs are counted, never
+ * clamped: *n_flagged (host, may be NULL; the call then synchronizes the stream) receives
+ * the number of pairs with |s_i - s_j| <= gap_tol * max(s_i, s_j) plus the number of
+ * s_i <= 2^-53 * s_0. */
+int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const double* S,
+                        const double* V, const double* gU, const double* gS, const double* gV,
+                        double* gA, double gap_tol, int* n_flagged);
+
+/* Synchronize the handle's stream and copy the stats of the last mpjsvd_svd call. */
+int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st);
+
+/* Free the workspace and the handle. */
+int mpjsvd_destroy(mpjsvd_handle h);
+
+/* Text of the last CUDA error seen by any call on this thread (static storage). */
+const char* mpjsvd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -6,8 +6,9 @@
  * leg are its only callers; the GPU library never links or calls it, and it shares no
  * code, header or table with the GPU library.
  *
- * Every routine is the textbook loop nest of the algorithm it cites, in IEEE binary64
- * (binary32 for the *_f32 routine), column-major, unblocked, single-threaded.
+ * Every routine is the textbook loop nest of the algorithm it cites, in the working
+ * precision orc_real (binary64 by default; binary32 for the *_f32 routine and the
+ * orthogonality test), column-major, unblocked, single-threaded.
  */
 #include "mpjsvd_oracle.h"
 
@@ -18,8 +19,16 @@
 
 #define AT(a, i, j, ld) ((a)[(size_t)(j) * (size_t)(ld) + (size_t)(i)])
 
-static const double U_WORK = 1.1102230246251565e-16; /* 2^-53, unit round-off of binary64 */
-static const double U_LOW = 5.9604644775390625e-08;  /* 2^-24, unit round-off of binary32 */
+#ifdef ORC_LONG_DOUBLE
+#define RSQRT sqrtl
+#define RFABS fabsl
+static const orc_real U_WORK = LDBL_EPSILON / 2;      /* unit round-off of long double */
+#else
+#define RSQRT sqrt
+#define RFABS fabs
+static const orc_real U_WORK = 1.1102230246251565e-16; /* 2^-53, unit round-off of binary64 */
+#endif
+static const orc_real U_LOW = 5.9604644775390625e-08;  /* 2^-24, unit round-off of binary32 */
 
 void orc_default_params(orc_params* p)
 {
@@ -27,17 +36,17 @@ void orc_default_params(orc_params* p)
     p->tol_orth = 1e-5;       /* Section 7.1 and the footnote of Section 3.5 */
     p->tol_cond_coef = 1.5;   /* Section 7.1: tol_cond = 1.5 n^(1/4) */
     p->trailing_frac = 0.25;  /* Section 3.5 footnote: check 1/4 to 1/3 of the columns */
-    p->tol = 0.0;             /* -> sqrt(n) * 2^-53 */
+    p->tol = 0.0;             /* -> RSQRT(n) * 2^-53 */
     p->maxsweep = 30;
     p->mode = 0;
     p->precond = 0;
 }
 
-static double nrm2(int len, const double* x)
+static orc_real nrm2(int len, const orc_real* x)
 {
-    double s = 0.0;
+    orc_real s = 0.0;
     for (int i = 0; i < len; ++i) s += x[i] * x[i];
-    return sqrt(s);
+    return RSQRT(s);
 }
 
 /* ---------------------------------------------------------------------------------
@@ -45,26 +54,26 @@ static double nrm2(int len, const double* x)
  * the switch, Section 3.3). H = I - tau v v^T, v[0] = 1, H x = beta e_1 with
  * beta = -sign(x_0) |x|, the choice that avoids cancellation in x_0 - beta.
  * ------------------------------------------------------------------------------- */
-void orc_house(int len, double* x, double* tau)
+void orc_house(int len, orc_real* x, orc_real* tau)
 {
     if (len <= 1) { *tau = 0.0; return; }
-    double alpha = x[0];
-    double s = 0.0;
+    orc_real alpha = x[0];
+    orc_real s = 0.0;
     for (int i = 1; i < len; ++i) s += x[i] * x[i];
     if (s == 0.0) { *tau = 0.0; return; } /* already a multiple of e_1: H = I */
-    double norm = sqrt(alpha * alpha + s);
-    double beta = (alpha >= 0.0) ? -norm : norm;
+    orc_real norm = RSQRT(alpha * alpha + s);
+    orc_real beta = (alpha >= 0.0) ? -norm : norm;
     *tau = (beta - alpha) / beta;
-    double den = alpha - beta;
+    orc_real den = alpha - beta;
     for (int i = 1; i < len; ++i) x[i] /= den; /* divide: a lone nonzero maps to +-1 exactly */
     x[0] = beta;
 }
 
 /* Apply H = I - tau v v^T (v[0] = 1 implicit, v[1..len-1] = vtail) to column c (len). */
-static void house_apply(int len, const double* vtail, double tau, double* c)
+static void house_apply(int len, const orc_real* vtail, orc_real tau, orc_real* c)
 {
     if (tau == 0.0) return;
-    double w = c[0];
+    orc_real w = c[0];
     for (int i = 1; i < len; ++i) w += vtail[i] * c[i];
     w *= tau;
     c[0] -= w;
@@ -72,12 +81,12 @@ static void house_apply(int len, const double* vtail, double tau, double* c)
 }
 
 /* Plain QR, A = Q0 R1 (Alg. 4 preprocessing for m > n; Section 3.1). */
-int orc_geqrf(int m, int n, double* A, int lda, double* tau)
+int orc_geqrf(int m, int n, orc_real* A, int lda, orc_real* tau)
 {
     if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
     int k = m < n ? m : n;
     for (int j = 0; j < k; ++j) {
-        double* colj = &AT(A, j, j, lda);
+        orc_real* colj = &AT(A, j, j, lda);
         orc_house(m - j, colj, &tau[j]);
         for (int c = j + 1; c < n; ++c) house_apply(m - j, colj, tau[j], &AT(A, j, c, lda));
     }
@@ -89,12 +98,12 @@ int orc_geqrf(int m, int n, double* A, int lda, double* tau)
  * eliminated by a Householder reflector. Column norms are downdated by the new row-j
  * entry and recomputed from scratch when the downdate has lost more than half the
  * digits (ratio test against the norm recorded at the last recomputation). */
-int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau)
+int orc_geqp3(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau)
 {
     if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
-    const double tol3z = sqrt(U_WORK);
-    double* vn1 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double* vn2 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    const orc_real tol3z = RSQRT(U_WORK);
+    orc_real* vn1 = (orc_real*)malloc(sizeof(orc_real) * (size_t)(n > 0 ? n : 1));
+    orc_real* vn2 = (orc_real*)malloc(sizeof(orc_real) * (size_t)(n > 0 ? n : 1));
     if (!vn1 || !vn2) { free(vn1); free(vn2); return -9; }
     for (int c = 0; c < n; ++c) {
         jpvt[c] = c;
@@ -108,7 +117,7 @@ int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau)
             if (vn1[c] > vn1[p]) p = c; /* first maximum wins ties */
         if (p != j) {
             for (int i = 0; i < m; ++i) {
-                double t = AT(A, i, j, lda);
+                orc_real t = AT(A, i, j, lda);
                 AT(A, i, j, lda) = AT(A, i, p, lda);
                 AT(A, i, p, lda) = t;
             }
@@ -116,20 +125,20 @@ int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau)
             vn1[p] = vn1[j];
             vn2[p] = vn2[j];
         }
-        double* colj = &AT(A, j, j, lda);
+        orc_real* colj = &AT(A, j, j, lda);
         orc_house(m - j, colj, &tau[j]);
         for (int c = j + 1; c < n; ++c) {
             house_apply(m - j, colj, tau[j], &AT(A, j, c, lda));
             if (vn1[c] != 0.0) {
-                double r = fabs(AT(A, j, c, lda)) / vn1[c];
-                double t = 1.0 - r * r;
+                orc_real r = RFABS(AT(A, j, c, lda)) / vn1[c];
+                orc_real t = 1.0 - r * r;
                 if (t < 0.0) t = 0.0;
-                double q = vn1[c] / vn2[c];
+                orc_real q = vn1[c] / vn2[c];
                 if (t * q * q <= tol3z) {
                     vn1[c] = (j + 1 < m) ? nrm2(m - j - 1, &AT(A, j + 1, c, lda)) : 0.0;
                     vn2[c] = vn1[c];
                 } else {
-                    vn1[c] *= sqrt(t);
+                    vn1[c] *= RSQRT(t);
                 }
             }
         }
@@ -139,13 +148,13 @@ int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau)
     return 0;
 }
 
-void orc_apply_q(int trans, int m, int ncols, int k, const double* V, int ldv,
-                 const double* tau, double* C, int ldc)
+void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
+                 const orc_real* tau, orc_real* C, int ldc)
 {
     /* Q = H_0 H_1 ... H_{k-1}: Q C applies H_{k-1} first, Q^T C applies H_0 first. */
     for (int s = 0; s < k; ++s) {
         int j = trans ? s : (k - 1 - s);
-        const double* v = &AT(V, j, j, ldv);
+        const orc_real* v = &AT(V, j, j, ldv);
         for (int c = 0; c < ncols; ++c) house_apply(m - j, v, tau[j], &AT(C, j, c, ldc));
     }
 }
@@ -156,22 +165,22 @@ void orc_apply_q(int trans, int m, int ncols, int k, const double* V, int ldv,
  * and x_p'^T x_q' = c^2 (gamma (1 - t^2) - t (beta - alpha)) with t = s / c. Setting it
  * to zero gives t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 gamma). Of its two
  * roots the one of modulus <= 1 gives the J closest to the identity (the footnote of
- * Section 2.1): t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).
+ * Section 2.1): t = sign(zeta) / (|zeta| + RSQRT(1 + zeta^2)).
  * ------------------------------------------------------------------------------- */
-double orc_rot_tangent(double alpha, double beta, double gamma)
+orc_real orc_rot_tangent(orc_real alpha, orc_real beta, orc_real gamma)
 {
-    double zeta = (beta - alpha) / (2.0 * gamma);
-    double az = fabs(zeta);
-    double t;
+    orc_real zeta = (beta - alpha) / (2.0 * gamma);
+    orc_real az = RFABS(zeta);
+    orc_real t;
     if (az > 1e150) t = 1.0 / (2.0 * az); /* zeta^2 would overflow; t -> 1/(2|zeta|) */
-    else t = 1.0 / (az + sqrt(1.0 + az * az));
+    else t = 1.0 / (az + RSQRT(1.0 + az * az));
     return (zeta >= 0.0) ? t : -t;
 }
 
 /* Alg. 1 in binary64. Cyclic order (1,2),(1,3),...,(n-1,n) of eq. (cyclic). The pair
  * (p, q) is rotated when |x_q^T x_p| > tol |x_p| |x_q|; a sweep without rotations
  * means convergence. alpha, beta, gamma are recomputed from the columns for each pair. */
-int orc_jacobi(int m, int n, double* X, int ldx, double* V, int ldv, int nv, double tol,
+int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
                int maxsweep, int* sweeps, long long* rotations)
 {
     long long rot = 0;
@@ -180,28 +189,28 @@ int orc_jacobi(int m, int n, double* X, int ldx, double* V, int ldv, int nv, dou
         converged = 1;
         for (int p = 0; p < n - 1; ++p) {
             for (int q = p + 1; q < n; ++q) {
-                double* xp = &AT(X, 0, p, ldx);
-                double* xq = &AT(X, 0, q, ldx);
-                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                orc_real* xp = &AT(X, 0, p, ldx);
+                orc_real* xq = &AT(X, 0, q, ldx);
+                orc_real alpha = 0.0, beta = 0.0, gamma = 0.0;
                 for (int i = 0; i < m; ++i) {
                     alpha += xp[i] * xp[i];
                     beta += xq[i] * xq[i];
                     gamma += xp[i] * xq[i];
                 }
-                if (!(fabs(gamma) > tol * sqrt(alpha) * sqrt(beta))) continue;
-                double t = orc_rot_tangent(alpha, beta, gamma);
-                double c = 1.0 / sqrt(1.0 + t * t);
-                double s = c * t;
+                if (!(RFABS(gamma) > tol * RSQRT(alpha) * RSQRT(beta))) continue;
+                orc_real t = orc_rot_tangent(alpha, beta, gamma);
+                orc_real c = 1.0 / RSQRT(1.0 + t * t);
+                orc_real s = c * t;
                 for (int i = 0; i < m; ++i) {
-                    double a = xp[i], b = xq[i];
+                    orc_real a = xp[i], b = xq[i];
                     xp[i] = c * a - s * b;
                     xq[i] = s * a + c * b;
                 }
                 if (V) {
-                    double* vp = &AT(V, 0, p, ldv);
-                    double* vq = &AT(V, 0, q, ldv);
+                    orc_real* vp = &AT(V, 0, p, ldv);
+                    orc_real* vq = &AT(V, 0, q, ldv);
                     for (int i = 0; i < nv; ++i) {
-                        double a = vp[i], b = vq[i];
+                        orc_real a = vp[i], b = vq[i];
                         vp[i] = c * a - s * b;
                         vq[i] = s * a + c * b;
                     }
@@ -262,7 +271,7 @@ int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int
 /* ---------------------------------------------------------------------------------
  * Algorithm 4.
  * ------------------------------------------------------------------------------- */
-static int all_finite(int m, int n, const double* A, int lda)
+static int all_finite(int m, int n, const orc_real* A, int lda)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < m; ++i)
@@ -271,23 +280,23 @@ static int all_finite(int m, int n, const double* A, int lda)
 }
 
 /* max_{i != j} |y_i^T y_j| / (|y_i| |y_j|): orthogonality of Y after the switch. */
-static double scaled_offdiag(int m, int n, const double* Y)
+static orc_real scaled_offdiag(int m, int n, const orc_real* Y)
 {
-    double worst = 0.0;
+    orc_real worst = 0.0;
     for (int p = 0; p < n; ++p) {
-        double np = nrm2(m, &AT(Y, 0, p, m));
+        orc_real np = nrm2(m, &AT(Y, 0, p, m));
         for (int q = p + 1; q < n; ++q) {
-            double nq = nrm2(m, &AT(Y, 0, q, m));
-            double g = 0.0;
+            orc_real nq = nrm2(m, &AT(Y, 0, q, m));
+            orc_real g = 0.0;
             for (int i = 0; i < m; ++i) g += AT(Y, i, p, m) * AT(Y, i, q, m);
-            double r = (np > 0.0 && nq > 0.0) ? fabs(g) / (np * nq) : 0.0;
+            orc_real r = (np > 0.0 && nq > 0.0) ? RFABS(g) / (np * nq) : 0.0;
             if (r > worst) worst = r;
         }
     }
     return worst;
 }
 
-int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, orc_real* V,
             const orc_params* pin, orc_stats* st)
 {
     orc_params p;
@@ -300,17 +309,17 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
     if (!all_finite(m, n, A, lda)) { s.status = 2; if (st) *st = s; return 2; }
 
     const size_t nn = (size_t)n * (size_t)n;
-    double* W0 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n); /* A, then Q0 \ R1 */
-    double* tau0 = (double*)malloc(sizeof(double) * (size_t)n);
-    double* R = (double*)calloc(nn, sizeof(double));                      /* R1, then Q1 \ R */
-    double* tau1 = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_real* W0 = (orc_real*)malloc(sizeof(orc_real) * (size_t)m * (size_t)n); /* A, then Q0 \ R1 */
+    orc_real* tau0 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
+    orc_real* R = (orc_real*)calloc(nn, sizeof(orc_real));                      /* R1, then Q1 \ R */
+    orc_real* tau1 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
     int* jpvt = (int*)malloc(sizeof(int) * (size_t)n);
-    double* X = (double*)calloc(nn, sizeof(double));
-    double* Y = (double*)malloc(sizeof(double) * nn);
-    double* Vacc = (double*)calloc(nn, sizeof(double));
-    double* Ux = (double*)calloc((size_t)m * (size_t)n, sizeof(double));
+    orc_real* X = (orc_real*)calloc(nn, sizeof(orc_real));
+    orc_real* Y = (orc_real*)malloc(sizeof(orc_real) * nn);
+    orc_real* Vacc = (orc_real*)calloc(nn, sizeof(orc_real));
+    orc_real* Ux = (orc_real*)calloc((size_t)m * (size_t)n, sizeof(orc_real));
     int* order = (int*)malloc(sizeof(int) * (size_t)n);
-    double* sig = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_real* sig = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
     if (!W0 || !tau0 || !R || !tau1 || !jpvt || !X || !Y || !Vacc || !Ux || !order || !sig) {
         s.status = -9;
         goto done;
@@ -337,18 +346,18 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
 
     /* Special cases of Section 3.5. */
     {
-        double rnn = fabs(AT(X, n - 1, n - 1, n));
-        s.cond_r = (rnn > 0.0) ? fabs(AT(X, 0, 0, n)) / rnn : INFINITY;
-        double tol_cond = p.tol_cond_coef * pow((double)n, 0.25);
-        double maxnorm = 0.0;
+        orc_real rnn = RFABS(AT(X, n - 1, n - 1, n));
+        s.cond_r = (rnn > 0.0) ? RFABS(AT(X, 0, 0, n)) / rnn : INFINITY;
+        orc_real tol_cond = p.tol_cond_coef * pow((orc_real)n, 0.25);
+        orc_real maxnorm = 0.0;
         for (int j = 0; j < n; ++j) {
-            double c = nrm2(n, &AT(X, 0, j, n));
+            orc_real c = nrm2(n, &AT(X, 0, j, n));
             if (c > maxnorm) maxnorm = c;
         }
-        int ntrail = (int)ceil(p.trailing_frac * (double)n);
+        int ntrail = (int)ceil(p.trailing_frac * (orc_real)n);
         int trailing_small = ntrail > 0;
         for (int j = n - ntrail; j < n; ++j)
-            if (nrm2(n, &AT(X, 0, j, n)) > sqrt(U_LOW) * maxnorm) trailing_small = 0;
+            if (nrm2(n, &AT(X, 0, j, n)) > RSQRT(U_LOW) * maxnorm) trailing_small = 0;
         /* orth = |Xt^T Xt - I|_max, Xt = low(X) D^-1, in binary32. */
         float* Xt = (float*)malloc(sizeof(float) * nn);
         if (!Xt) { s.status = -9; goto done; }
@@ -382,11 +391,11 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
         /* Lower-precision SVD of low(X), U only (Section 3.2). The paper would use QR-SVD
          * when orth > tol_alg; this oracle always uses Alg. 1 (Jacobi). */
         float* Xl = (float*)malloc(sizeof(float) * nn);
-        double* B = (double*)malloc(sizeof(double) * nn);
-        double* tau2 = (double*)malloc(sizeof(double) * (size_t)n);
+        orc_real* B = (orc_real*)malloc(sizeof(orc_real) * nn);
+        orc_real* tau2 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
         if (!Xl || !B || !tau2) { free(Xl); free(B); free(tau2); s.status = -9; goto done; }
         for (size_t i = 0; i < nn; ++i) Xl[i] = (float)X[i];
-        orc_jacobi_f32(n, n, Xl, n, (float)(sqrt((double)n) * U_LOW), p.maxsweep, &s.sweeps_low,
+        orc_jacobi_f32(n, n, Xl, n, (float)(RSQRT((orc_real)n) * U_LOW), p.maxsweep, &s.sweeps_low,
                        &s.rot_low);
         /* U_low = normalized columns sorted by descending norm (Alg. 1 final loop and
          * sort), promoted to binary64. The sort matters for the switch: the QR of
@@ -408,12 +417,12 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
             while (b >= 0 && sl[ord[b]] < sl[oj]) { ord[b + 1] = ord[b]; --b; }
             ord[b + 1] = oj;
         }
-        /* Switch (Section 3.3, method preferred there): B = X^T double(U_low),
+        /* Switch (Section 3.3, method preferred there): B = X^T orc_real(U_low),
          * B = Q R2, Y = X Q; the refinement's V accumulator starts at Q. */
         for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) {
-                double acc = 0.0;
-                for (int i = 0; i < n; ++i) acc += AT(X, i, a, n) * (double)AT(Xl, i, ord[b], n);
+                orc_real acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += AT(X, i, a, n) * (orc_real)AT(Xl, i, ord[b], n);
                 AT(B, a, b, n) = acc;
             }
         free(sl);
@@ -423,7 +432,7 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
         orc_apply_q(0, n, n, n, B, n, tau2, Vacc, n); /* Vacc = Q */
         for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) {
-                double acc = 0.0;
+                orc_real acc = 0.0;
                 for (int i = 0; i < n; ++i) acc += AT(X, a, i, n) * AT(Vacc, i, b, n);
                 AT(Y, a, b, n) = acc;
             }
@@ -432,14 +441,14 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
         free(B);
         free(tau2);
     } else {
-        memcpy(Y, X, sizeof(double) * nn);
+        memcpy(Y, X, sizeof(orc_real) * nn);
         for (int j = 0; j < n; ++j) AT(Vacc, j, j, n) = 1.0;
         s.switch_off = scaled_offdiag(n, n, Y);
     }
 
     /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated. */
     {
-        double tol = (p.tol > 0.0) ? p.tol : sqrt((double)n) * U_WORK;
+        orc_real tol = (p.tol > 0.0) ? p.tol : RSQRT((orc_real)n) * U_WORK;
         int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, &s.sweeps_work, &s.rot_work);
         if (rc != 0) s.status = 1;
     }
@@ -461,9 +470,9 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
         int j = order[k];
         S[k] = sig[j];
         for (int i = 0; i < n; ++i) {
-            double ux = (sig[j] > 0.0) ? AT(Y, i, j, n) / sig[j] : 0.0;
-            double uR = (p.precond == 1) ? ux : AT(Vacc, i, j, n);
-            double vR = (p.precond == 1) ? AT(Vacc, i, j, n) : ux;
+            orc_real ux = (sig[j] > 0.0) ? AT(Y, i, j, n) / sig[j] : 0.0;
+            orc_real uR = (p.precond == 1) ? ux : AT(Vacc, i, j, n);
+            orc_real vR = (p.precond == 1) ? AT(Vacc, i, j, n) : ux;
             AT(Ux, i, k, m) = uR;
             /* V = P V_R: row jpvt[i] of V is row i of V_R (Alg. 2, V <- P V_X). */
             AT(V, jpvt[i], k, n) = vR;
@@ -476,8 +485,8 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
     for (int k = 0; k < n; ++k) {
         int r = 0;
         for (int i = 1; i < n; ++i)
-            if (fabs(AT(V, i, k, n)) > fabs(AT(V, r, k, n))) r = i;
-        double sgn = (AT(V, r, k, n) < 0.0) ? -1.0 : 1.0;
+            if (RFABS(AT(V, i, k, n)) > RFABS(AT(V, r, k, n))) r = i;
+        orc_real sgn = (AT(V, r, k, n) < 0.0) ? -1.0 : 1.0;
         for (int i = 0; i < n; ++i) AT(V, i, k, n) *= sgn;
         for (int i = 0; i < m; ++i) AT(U, i, k, m) = sgn * AT(Ux, i, k, m);
     }
@@ -498,53 +507,53 @@ done:
  *   gA = U [ (F o (U^T gU - gU^T U)) S + diag(gS) + S (F o (V^T gV - gV^T V)) ] V^T
  *        + (I - U U^T) gU S^-1 V^T.
  * ------------------------------------------------------------------------------- */
-int orc_svd_backward(int m, int n, const double* U, const double* S, const double* V,
-                     const double* gU, const double* gS, const double* gV, double* gA,
-                     double gap_tol, int* n_flagged)
+int orc_svd_backward(int m, int n, const orc_real* U, const orc_real* S, const orc_real* V,
+                     const orc_real* gU, const orc_real* gS, const orc_real* gV, orc_real* gA,
+                     orc_real gap_tol, int* n_flagged)
 {
     if (n < 1 || m < n) return -1;
     const size_t nn = (size_t)n * (size_t)n;
-    double* M1 = (double*)calloc(nn, sizeof(double)); /* U^T gU */
-    double* M2 = (double*)calloc(nn, sizeof(double)); /* V^T gV */
-    double* K = (double*)calloc(nn, sizeof(double));
-    double* T = (double*)calloc((size_t)m * (size_t)n, sizeof(double));
+    orc_real* M1 = (orc_real*)calloc(nn, sizeof(orc_real)); /* U^T gU */
+    orc_real* M2 = (orc_real*)calloc(nn, sizeof(orc_real)); /* V^T gV */
+    orc_real* K = (orc_real*)calloc(nn, sizeof(orc_real));
+    orc_real* T = (orc_real*)calloc((size_t)m * (size_t)n, sizeof(orc_real));
     if (!M1 || !M2 || !K || !T) { free(M1); free(M2); free(K); free(T); return -9; }
     int flagged = 0;
     for (int i = 0; i < n; ++i) {
         if (S[i] <= U_WORK * S[0]) ++flagged;
         for (int j = i + 1; j < n; ++j) {
-            double big = S[i] > S[j] ? S[i] : S[j];
-            if (fabs(S[i] - S[j]) <= gap_tol * big) ++flagged;
+            orc_real big = S[i] > S[j] ? S[i] : S[j];
+            if (RFABS(S[i] - S[j]) <= gap_tol * big) ++flagged;
         }
     }
     if (gU)
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
-                double acc = 0.0;
+                orc_real acc = 0.0;
                 for (int r = 0; r < m; ++r) acc += AT(U, r, i, m) * AT(gU, r, j, m);
                 AT(M1, i, j, n) = acc;
             }
     if (gV)
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
-                double acc = 0.0;
+                orc_real acc = 0.0;
                 for (int r = 0; r < n; ++r) acc += AT(V, r, i, n) * AT(gV, r, j, n);
                 AT(M2, i, j, n) = acc;
             }
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
             if (i == j) { AT(K, i, i, n) = gS ? gS[i] : 0.0; continue; }
-            double f = 1.0 / (S[j] * S[j] - S[i] * S[i]);
+            orc_real f = 1.0 / (S[j] * S[j] - S[i] * S[i]);
             AT(K, i, j, n) = f * (AT(M1, i, j, n) - AT(M1, j, i, n)) * S[j] +
                              S[i] * f * (AT(M2, i, j, n) - AT(M2, j, i, n));
         }
     /* T = U K + (gU - U M1) S^-1 */
     for (int j = 0; j < n; ++j)
         for (int r = 0; r < m; ++r) {
-            double acc = 0.0;
+            orc_real acc = 0.0;
             for (int i = 0; i < n; ++i) acc += AT(U, r, i, m) * AT(K, i, j, n);
             if (gU) {
-                double proj = 0.0;
+                orc_real proj = 0.0;
                 for (int i = 0; i < n; ++i) proj += AT(U, r, i, m) * AT(M1, i, j, n);
                 acc += (AT(gU, r, j, m) - proj) / S[j];
             }
@@ -553,7 +562,7 @@ int orc_svd_backward(int m, int n, const double* U, const double* S, const doubl
     /* gA = T V^T */
     for (int c = 0; c < n; ++c)
         for (int r = 0; r < m; ++r) {
-            double acc = 0.0;
+            orc_real acc = 0.0;
             for (int j = 0; j < n; ++j) acc += AT(T, r, j, m) * AT(V, c, j, n);
             AT(gA, r, c, m) = acc;
         }

@@ -8,8 +8,8 @@
  *
  * All matrices are column-major (LAPACK convention): element (i, j) of a matrix
  * with leading dimension ld lives at a[j * ld + i]. Arithmetic is IEEE binary64
- * unless a function name ends in _f32 (binary32 loops, used for the paper's
- * lower-precision stage). Nothing is blocked, fused or reordered beyond what the
+ * (orc_real, see below) unless a function name ends in _f32 (binary32 loops, used for
+ * the paper's lower-precision stage). Nothing is blocked, fused or reordered beyond what the
  * paper's algorithms state.
  */
 #ifndef MPJSVD_ORACLE_H
@@ -19,13 +19,23 @@
 extern "C" {
 #endif
 
+/* Working precision. The default build is IEEE binary64, the precision of the method.
+ * The same source compiled with -DORC_LONG_DOUBLE uses long double (x86-64: 64-bit
+ * significand; aarch64: IEEE binary128) as an extended-precision reference that
+ * attributes rounding error; the binary32 stage stays binary32 in both builds. */
+#ifdef ORC_LONG_DOUBLE
+typedef long double orc_real;
+#else
+typedef double orc_real;
+#endif
+
 /* Tunables of Algorithm 4 (Section 3, values used in Section 7.1). */
 typedef struct {
-    double tol_alg;        /* Jacobi vs QR-SVD choice threshold (Alg. 4), default 1e-2 */
-    double tol_orth;       /* orthogonality skip threshold (Section 3.5), default 1e-5 */
-    double tol_cond_coef;  /* tol_cond = coef * n^(1/4) (Section 7.1), default 1.5 */
-    double trailing_frac;  /* fraction of trailing columns tested (Section 3.5), default 0.25 */
-    double tol;            /* Alg. 1 threshold in working precision; <= 0 -> sqrt(n) * 2^-53 */
+    orc_real tol_alg;        /* Jacobi vs QR-SVD choice threshold (Alg. 4), default 1e-2 */
+    orc_real tol_orth;       /* orthogonality skip threshold (Section 3.5), default 1e-5 */
+    orc_real tol_cond_coef;  /* tol_cond = coef * n^(1/4) (Section 7.1), default 1.5 */
+    orc_real trailing_frac;  /* fraction of trailing columns tested (Section 3.5), default 0.25 */
+    orc_real tol;            /* Alg. 1 threshold in working precision; <= 0 -> sqrt(n) * 2^-53 */
     int maxsweep;          /* Alg. 1 maxiter, default 30 */
     int mode;              /* 0 auto (Alg. 4 branch tests), 1 force the low-precision stage,
                               2 never run it (plain FP64 preconditioned Jacobi, Alg. 2) */
@@ -43,9 +53,9 @@ typedef struct {
     int sweeps_work;       /* FP64 Alg. 1 sweeps */
     long long rot_low;     /* rotations applied in FP32 */
     long long rot_work;    /* rotations applied in FP64 */
-    double cond_r;         /* |R(0,0)| / |R(n-1,n-1)| */
-    double orth;           /* max |Xt^T Xt - I| of the column-scaled low(X), FP32 */
-    double switch_off;     /* max_{i!=j} |y_i^T y_j| / (|y_i||y_j|) right after the switch */
+    orc_real cond_r;         /* |R(0,0)| / |R(n-1,n-1)| */
+    orc_real orth;           /* max |Xt^T Xt - I| of the column-scaled low(X), FP32 */
+    orc_real switch_off;     /* max_{i!=j} |y_i^T y_j| / (|y_i||y_j|) right after the switch */
     int status;            /* 0 ok, 1 FP64 sweeps hit maxsweep, 2 non-finite input, <0 bad argument */
 } orc_stats;
 
@@ -54,26 +64,26 @@ void orc_default_params(orc_params* p);
 /* Householder reflector (Section 3.1): overwrite x[0..len-1] (stride 1) so that
  * x[0] = beta and x[1..] = v[1..] with v[0] = 1 implicit and H = I - tau v v^T,
  * H * x_in = beta * e_1. */
-void orc_house(int len, double* x, double* tau);
+void orc_house(int len, orc_real* x, orc_real* tau);
 
 /* Plain Householder QR, A = Q R (Alg. 4, the m > n preprocessing). In place: R in
  * the upper triangle, reflectors below it, tau[min(m,n)]. */
-int orc_geqrf(int m, int n, double* A, int lda, double* tau);
+int orc_geqrf(int m, int n, orc_real* A, int lda, orc_real* tau);
 
 /* Businger-Golub QR with column pivoting, A P = Q R (Section 3.1, Alg. 5 step 2).
  * jpvt[i] = original index of the column in position i (0-based). Column norms are
  * downdated after each step and recomputed when cancellation is severe. */
-int orc_geqp3(int m, int n, double* A, int lda, int* jpvt, double* tau);
+int orc_geqp3(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau);
 
 /* C <- Q C (trans = 0) or Q^T C (trans = 1), Q = H_0 H_1 ... H_{k-1} from orc_geqrf /
  * orc_geqp3 output (V, ldv, tau). C is m x ncols. */
-void orc_apply_q(int trans, int m, int ncols, int k, const double* V, int ldv,
-                 const double* tau, double* C, int ldc);
+void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
+                 const orc_real* tau, orc_real* C, int ldc);
 
 /* Alg. 1 in binary64: cyclic one-sided Jacobi on X (m x n). If V != NULL, every rotation
  * is also applied to the columns of V (nv x n). Returns 0 if converged, 1 if maxsweep
  * sweeps ran without converging. */
-int orc_jacobi(int m, int n, double* X, int ldx, double* V, int ldv, int nv, double tol,
+int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
                int maxsweep, int* sweeps, long long* rotations);
 
 /* Alg. 1 in binary32, no V (Alg. 4: "without generating V explicitly"). */
@@ -83,13 +93,13 @@ int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int
 /* Jacobi rotation for one column pair (Section 2.1): given alpha = |x_p|^2,
  * beta = |x_q|^2, gamma = x_p^T x_q (gamma != 0), the tangent t of the rotation closest
  * to the identity that makes [x_p, x_q] J orthogonal, J = [c s; -s c], s = c t. */
-double orc_rot_tangent(double alpha, double beta, double gamma);
+orc_real orc_rot_tangent(orc_real alpha, orc_real beta, orc_real gamma);
 
 /* Algorithm 4 (with Algorithm 2 as its mode-2 special case): thin SVD of A (m x n,
  * m >= n). U m x n (ldu = m), S n (descending), V n x n (ldv = n), A = U diag(S) V^T.
  * Sign convention: each (u_i, v_i) is flipped so that the entry of v_i with the largest
  * magnitude (lowest row index on ties) is positive. */
-int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, orc_real* V,
             const orc_params* p, orc_stats* st);
 
 /* Adjoint of the thin SVD (not in the paper; published SVD-derivative formula).
@@ -97,9 +107,9 @@ int orc_svd(int m, int n, const double* A, int lda, double* U, double* S, double
  * (each may be NULL = zero), writes gA (m x n). Pairs with
  * |s_i - s_j| <= gap_tol * max(s_i, s_j) and singular values s_i <= 2^-53 * s_0 are
  * counted in *n_flagged; nothing is clamped. */
-int orc_svd_backward(int m, int n, const double* U, const double* S, const double* V,
-                     const double* gU, const double* gS, const double* gV, double* gA,
-                     double gap_tol, int* n_flagged);
+int orc_svd_backward(int m, int n, const orc_real* U, const orc_real* S, const orc_real* V,
+                     const orc_real* gU, const orc_real* gS, const orc_real* gV, orc_real* gA,
+                     orc_real gap_tol, int* n_flagged);
 
 #ifdef __cplusplus
 }

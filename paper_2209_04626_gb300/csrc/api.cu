@@ -1,0 +1,207 @@
+// api.cu -- the extern "C" entry points declared in include/mpjsvd.h: argument validation,
+// the handle and its workspace; the work itself is in svd_single.cu, svd_batched.cu and
+// adjoint.cu.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mpj {
+
+static thread_local char g_last_error[256] = "no error";
+
+void set_last_error(const char* where, cudaError_t e)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+}
+
+int cuda_fail(const char* where, cudaError_t e)
+{
+    set_last_error(where, e);
+    return MPJSVD_ERR_CUDA;
+}
+
+int ensure_buffer(void** buf, size_t* cur, size_t bytes)
+{
+    if (*buf && *cur >= bytes) return 0;
+    if (*buf) {
+        cudaError_t e = cudaFree(*buf);
+        *buf = nullptr;
+        *cur = 0;
+        if (e != cudaSuccess) return cuda_fail("workspace free", e);
+    }
+    cudaError_t e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        set_last_error("workspace cudaMalloc", e);
+        cudaGetLastError();
+        return MPJSVD_ERR_NOMEM;
+    }
+    *cur = bytes;
+    return 0;
+}
+
+}  // namespace mpj
+
+using namespace mpj;
+
+extern "C" {
+
+int mpjsvd_default_params(mpjsvd_params* p)
+{
+    if (!p) return -1;
+    p->tol_alg = 1e-2;
+    p->tol_orth = 1e-5;
+    p->tol_cond_coef = 1.5;
+    p->trailing_frac = 0.25;
+    p->maxsweep = 30;
+    p->block_w = 0;
+    p->mode = MPJSVD_MODE_AUTO;
+    p->precond = MPJSVD_PRECOND_RT;
+    p->qr_first = 0;
+    p->timing = 0;
+    return 0;
+}
+
+static int check_params(const mpjsvd_params* p)
+{
+    if (p->maxsweep < 1 || p->maxsweep > 64) return 1;
+    if (p->block_w < 0 || p->block_w > 16) return 1;
+    if (p->mode < 0 || p->mode > 2) return 1;
+    if (p->precond < 0 || p->precond > 1) return 1;
+    if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
+    return 0;
+}
+
+int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream)
+{
+    if (!h) return -1;
+    *h = nullptr;
+    mpjsvd_params prm;
+    if (p) prm = *p;
+    else mpjsvd_default_params(&prm);
+    if (check_params(&prm)) return -2;
+    mpjsvd_ctx* c = new (std::nothrow) mpjsvd_ctx();
+    if (!c) return MPJSVD_ERR_NOMEM;
+    memset(c, 0, sizeof(*c));
+    c->params = prm;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { delete c; return cuda_fail("cudaGetDevice", e); }
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) { delete c; return cuda_fail("SM count", e); }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (!coop) { delete c; return cuda_fail("cooperative launch unsupported", cudaErrorNotSupported); }
+    e = cudaMalloc(&c->dstate, sizeof(DevState));
+    if (e != cudaSuccess) { delete c; set_last_error("state cudaMalloc", e); return MPJSVD_ERR_NOMEM; }
+    c->have_events = true;
+    for (int i = 0; i < 8; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
+    *h = c;
+    return 0;
+}
+
+int mpjsvd_set_stream(mpjsvd_handle h, void* cuda_stream)
+{
+    if (!h) return -1;
+    h->stream = (cudaStream_t)cuda_stream;
+    return 0;
+}
+
+int mpjsvd_set_params(mpjsvd_handle h, const mpjsvd_params* p)
+{
+    if (!h) return -1;
+    if (!p || check_params(p)) return -2;
+    h->params = *p;
+    return 0;
+}
+
+int mpjsvd_svd(mpjsvd_handle h, int m, int n, const double* A, int lda, double* U, double* S,
+               double* V, double tol)
+{
+    if (!h) return -1;
+    if (m < 1 || m < n || m > 24576) return -2;
+    if (n < 1 || n > 12288) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (!U) return -6;
+    if (!S) return -7;
+    if (!V) return -8;
+    if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -9;
+    int d = -1;
+    cudaGetDevice(&d);
+    if (d != h->device) return cuda_fail("mpjsvd_svd: current device differs from the handle's", cudaErrorInvalidDevice);
+    int rc = svd_single(h, m, n, A, lda, U, S, V, tol);
+    h->last_valid = (rc == 0);
+    return rc;
+}
+
+int mpjsvd_svd_batched(mpjsvd_handle h, int batch, const int* m, const int* n, const int* lda,
+                       const double* const* A, double* const* U, double* const* S,
+                       double* const* V, double tol, int* info)
+{
+    if (!h) return -1;
+    if (batch < 0) return -2;
+    if (batch == 0) return 0;
+    if (!m) return -3;
+    if (!n) return -4;
+    if (!lda) return -5;
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] < 1 || n[i] > 512) return -4;
+        if (m[i] < n[i] || m[i] > 1024) return -3;
+        if (lda[i] < m[i]) return -5;
+    }
+    if (!A) return -6;
+    if (!U) return -7;
+    if (!S) return -8;
+    if (!V) return -9;
+    if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -10;
+    if (!info) return -11;
+    return svd_batched(h, batch, m, n, lda, A, U, S, V, tol, info);
+}
+
+int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const double* S,
+                        const double* V, const double* gU, const double* gS, const double* gV,
+                        double* gA, double gap_tol, int* n_flagged)
+{
+    if (!h) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (!U) return -4;
+    if (!S) return -5;
+    if (!V) return -6;
+    if (!gA) return -10;
+    if (!(gap_tol >= 0.0)) return -11;
+    return svd_backward(h, m, n, U, S, V, gU, gS, gV, gA, gap_tol, n_flagged);
+}
+
+int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st)
+{
+    if (!h) return -1;
+    if (!st) return -2;
+    return read_stats(h, st);
+}
+
+int mpjsvd_destroy(mpjsvd_handle h)
+{
+    if (!h) return -1;
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->bws) cudaFree(h->bws);
+    if (h->aws) cudaFree(h->aws);
+    if (h->dstate) cudaFree(h->dstate);
+    if (h->have_events)
+        for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
+    delete h;
+    return 0;
+}
+
+const char* mpjsvd_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// common.cuh -- device helpers shared by the mpjsvd kernels (sm_103a).
+//
+// Matrices are column-major FP64 (LAPACK convention) unless a name says otherwise.
+// Every wait in device code is bounded in time: a grid barrier gives up after
+// kSpinLimitNs, records MPJSVD_STATUS_TIMEOUT in the call's status word and returns
+// false, so the kernel can exit and the context stays usable.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpjsvd.h"
+
+namespace mpj {
+
+constexpr int kWarp = 32;
+constexpr uint64_t kSpinLimitNs = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Per-call device state: barrier words, the status word and counters. Zeroed by the
+// host at the start of every call (one cudaMemsetAsync).
+struct DevState {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int status;            // MPJSVD_STATUS_* bits set by device code (atomicOr)
+    int gate_low;          // 1: run the lower-precision stage (Alg. 4 branch decision)
+    int branch;            // mpjsvd_stats.branch
+    int sweeps_low;
+    int sweeps_work;
+    int pad0;
+    unsigned long long rot_low;
+    unsigned long long rot_work;
+    double cond_r;
+    double orth;
+    double maxnorm;        // max column norm of X (branch test)
+    unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
+    int argmax_idx[512];                   // QRCP: per-CTA candidate pivot
+    double argmax_val[512];
+};
+
+// Bounded grid barrier for a cooperative launch (all CTAs co-resident). Returns false
+// if the wait timed out or another CTA reported an error; callers then exit.
+__device__ __forceinline__ bool grid_sync(DevState* st)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &st->bar_gen;
+        unsigned int gen = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            st->bar_count = 0;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned int spins = 0;
+            while (*vgen == gen) {
+                if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kSpinLimitNs) {
+                    atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A "group" is the set of CTAs that cooperate on one matrix: all CTAs of a cooperative
+// launch (single-matrix path) or one CTA (batched path, where sync is __syncthreads).
+struct Group {
+    int rank;        // this CTA's index in the group
+    int size;        // number of CTAs in the group
+    DevState* st;    // barrier/status state (single-matrix path), may be null if size == 1
+    __device__ __forceinline__ bool sync() const
+    {
+        if (size == 1) {
+            __syncthreads();
+            return true;
+        }
+        return grid_sync(st);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA; every thread gets the result. scratch: >= 32 elements of T.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T r = (lane < nw) ? scratch[lane] : T(0);
+    r = warp_sum(r);
+    return r;
+}
+
+__device__ __forceinline__ size_t cm(int i, int j, int ld) { return (size_t)j * (size_t)ld + (size_t)i; }
+
+}  // namespace mpj

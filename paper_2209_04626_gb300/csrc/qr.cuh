@@ -1,0 +1,347 @@
+// qr.cuh -- Householder QR and QR with column pivoting (Section 3.1 of the paper; the
+// QRCP is the Businger-Golub RRQR the paper takes from DGEQP3), and the application of
+// the resulting orthogonal factor.
+//
+// Parallel form: physical column c of the m x n matrix is owned by CTA c % g.size; every
+// CTA recomputes the step's Householder vector from the pivot column (identical
+// arithmetic in every CTA, so no broadcast is needed) and updates only its own columns.
+// One group barrier per step (before the pivot is chosen). Pivoting is logical: columns never move; perm[j] names
+// the physical column eliminated at step j, and a final gather puts R and the reflectors
+// in logical order.
+#pragma once
+
+#include "common.cuh"
+
+namespace mpj {
+
+constexpr int kQrColBatch = 4;     // owned columns reduced together per pass
+constexpr int kQrSlotStride = 256; // pivot-candidate slots per step parity (max CTAs)
+constexpr int kApplyBatch = 8;     // columns of C updated per pass of apply_q_cols
+
+// Householder vector of x = A(j:m-1, p) into vs[j..m-1] (vs[j] = 1), returns tau and beta.
+// H = I - tau v v^T, H x = beta e_1, beta = -sign(x_0) |x|. The tail is divided (not
+// multiplied by a reciprocal) by x_0 - beta.
+__device__ __forceinline__ void house_vector(int m, int j, const double* __restrict__ col,
+                                             double* vs, double* red, double& tau, double& beta)
+{
+    // the pivot column was last written by its owner CTA: read through L2 (__ldcg), never
+    // from a possibly stale L1 line
+    double s = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        double x = __ldcg(col + i);
+        vs[i] = x;
+        s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    double alpha = __ldcg(col + j);
+    if (s == 0.0) {
+        tau = 0.0;
+        beta = alpha;
+    } else {
+        double nrm = sqrt(fma(alpha, alpha, s));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        double den = alpha - beta;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) vs[i] = vs[i] / den;
+    }
+    if (threadIdx.x == 0) vs[j] = 1.0;
+    __syncthreads();
+}
+
+// Partial dot products of v (rows j..m-1) with up to kQrColBatch columns, reduced over the
+// CTA. red must hold >= kQrColBatch * 32 doubles. Result in w[] (all threads).
+__device__ __forceinline__ void batch_dots(int m, int j, const double* vs, double* const* cols,
+                                           int nb, double* red, double* w)
+{
+    double acc[kQrColBatch];
+#pragma unroll
+    for (int b = 0; b < kQrColBatch; ++b) acc[b] = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        double vi = vs[i];
+#pragma unroll
+        for (int b = 0; b < kQrColBatch; ++b)
+            if (b < nb) acc[b] = fma(vi, cols[b][i], acc[b]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int b = 0; b < kQrColBatch; ++b) acc[b] = warp_sum(acc[b]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < kQrColBatch; ++b) red[b * 32 + wid] = acc[b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < kQrColBatch; ++b) {
+        double r = (lane < nw) ? red[b * 32 + lane] : 0.0;
+        w[b] = warp_sum(r);
+    }
+}
+
+// Column-distributed Householder QR (PIVOT = false) or QR with column pivoting
+// (PIVOT = true) of the m x n matrix A (m >= n), in place.
+// Outputs: tau[j]; perm[j] = physical column eliminated at step j (identity if !PIVOT);
+// physical column perm[j] holds R(0..j, j) in rows 0..j and the reflector tail in rows
+// j+1..m-1. Per-column metadata of the CTA's own columns (active flag, norms, new row-j
+// entry) lives in shared memory. Dynamic shared memory: vs[m] doubles followed by
+// own_max * (3 doubles + 1 int), own_max = ceil(n / g.size) (see hh_qr_smem_bytes).
+// Returns false if a group barrier failed (the caller must exit).
+__host__ __device__ inline size_t hh_qr_smem_bytes(int m, int n, int gsize)
+{
+    int own = (n + gsize - 1) / gsize;
+    return sizeof(double) * ((size_t)m + 3 * (size_t)own) + sizeof(int) * (size_t)own + 64;
+}
+
+template <bool PIVOT>
+__device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* tau, int* perm,
+                      double* smem)
+{
+    __shared__ double red[kQrColBatch * 32];
+    __shared__ int s_piv;
+    __shared__ int s_recompute;
+    const double tol3z = 1.0536712127723509e-08;  // sqrt(2^-53)
+    DevState* st = g.st;
+    const int own = (n - g.rank + g.size - 1) / g.size;  // columns c = rank + t * size
+    double* vs = smem;
+    double* vn1 = vs + m;
+    double* vn2 = vn1 + own;
+    double* rowj = vn2 + own;
+    int* act = (int*)(rowj + own);
+    const int lane = threadIdx.x & 31;
+
+    for (int t = threadIdx.x; t < own; t += blockDim.x) act[t] = 1;
+    if (PIVOT) {
+        // initial norms of the CTA's columns
+        for (int t = 0; t < own; ++t) {
+            const double* col = A + cm(0, g.rank + t * g.size, lda);
+            double s = 0.0;
+            for (int i = threadIdx.x; i < m; i += blockDim.x) s = fma(col[i], col[i], s);
+            s = block_sum(s, red);
+            if (threadIdx.x == 0) {
+                vn1[t] = sqrt(s);
+                vn2[t] = vn1[t];
+            }
+        }
+    }
+    __syncthreads();
+
+    int prev_p = -1;       // pivot column of the previous step (its store is deferred)
+    double prev_beta = 0.0;
+    for (int j = 0; j < n; ++j) {
+        // ---- pivot column of this step
+        if (PIVOT) {
+            // this CTA's candidate (warp 0): largest norm among active columns, first
+            // active column if every comparison fails (NaN norms)
+            if (threadIdx.x < 32) {
+                int best = -1;
+                double bv = 0.0;
+                for (int t = lane; t < own; t += 32) {
+                    if (!act[t]) continue;
+                    double v = vn1[t];
+                    if (best < 0 || v > bv) { bv = v; best = t; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    if (ob >= 0 && (best < 0 || ov > bv || (ov == bv && ob < best))) { bv = ov; best = ob; }
+                }
+                // slots alternate with the step's parity, so a CTA that runs ahead writes
+                // step j+1's candidate while slower CTAs still read step j's
+                if (lane == 0) {
+                    st->argmax_val[(j & 1) * kQrSlotStride + g.rank] = bv;
+                    st->argmax_idx[(j & 1) * kQrSlotStride + g.rank] = best >= 0 ? g.rank + best * g.size : -1;
+                }
+            }
+            if (!g.sync()) return false;
+            if (threadIdx.x < 32) {
+                int best = -1;
+                double bv = 0.0;
+                for (int r = lane; r < g.size; r += 32) {
+                    double v = __ldcg(&st->argmax_val[(j & 1) * kQrSlotStride + r]);
+                    int idx = __ldcg(&st->argmax_idx[(j & 1) * kQrSlotStride + r]);
+                    if (idx >= 0 && (best < 0 || v > bv || (v == bv && idx < best))) { bv = v; best = idx; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, best, o);
+                    if (oi >= 0 && (best < 0 || ov > bv || (ov == bv && oi < best))) { bv = ov; best = oi; }
+                }
+                if (lane == 0) s_piv = best;
+            }
+            __syncthreads();
+        } else {
+            if (j > 0 && !g.sync()) return false;
+            if (threadIdx.x == 0) s_piv = j;
+            __syncthreads();
+        }
+        const int p = s_piv;
+        if (p < 0 || p >= n) {  // cannot happen: n - j >= 1 columns are active
+            if (threadIdx.x == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+            return false;
+        }
+        double* colp = A + cm(0, p, lda);
+
+        // ---- store of the previous step's reflector, deferred past the barrier because
+        //      every CTA reads the pivot column during its own step
+        if (prev_p >= 0 && prev_p % g.size == g.rank) {
+            double* cq = A + cm(0, prev_p, lda);
+            for (int i = j + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i];
+            if (threadIdx.x == 0) cq[j - 1] = prev_beta;
+        }
+        __syncthreads();
+
+        // ---- Householder vector, computed redundantly by every CTA
+        double tj, beta;
+        house_vector(m, j, colp, vs, red, tj, beta);
+
+        if (p % g.size == g.rank) {
+            if (threadIdx.x == 0) {
+                tau[j] = tj;
+                perm[j] = p;
+                act[(p - g.rank) / g.size] = 0;
+            }
+        }
+        prev_p = p;
+        prev_beta = beta;
+        __syncthreads();
+
+        // ---- apply H_j to this CTA's active columns, kQrColBatch at a time
+        int t = 0;
+        while (true) {
+            double* cols[kQrColBatch];
+            int tix[kQrColBatch];
+            int nb = 0;
+            for (; t < own && nb < kQrColBatch; ++t) {
+                int c = g.rank + t * g.size;
+                bool active = PIVOT ? (act[t] != 0) : (c > j);
+                if (active) {
+                    tix[nb] = t;
+                    cols[nb] = A + cm(0, c, lda);
+                    ++nb;
+                }
+            }
+            if (nb == 0) break;
+            for (int b = nb; b < kQrColBatch; ++b) { cols[b] = cols[0]; tix[b] = tix[0]; }
+            if (tj != 0.0) {
+                double w[kQrColBatch];
+                batch_dots(m, j, vs, cols, nb, red, w);
+                for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+                    double vi = vs[i];
+#pragma unroll
+                    for (int b = 0; b < kQrColBatch; ++b)
+                        if (b < nb) {
+                            double nv = fma(-tj * w[b], vi, cols[b][i]);
+                            cols[b][i] = nv;
+                            if (PIVOT && i == j) rowj[tix[b]] = nv;
+                        }
+                }
+            } else if (PIVOT && threadIdx.x == 0) {
+                for (int b = 0; b < nb; ++b) rowj[tix[b]] = cols[b][j];
+            }
+            __syncthreads();
+            if (PIVOT) {
+                // downdate the norms by the new row-j entries, one thread per column;
+                // recompute from the data when cancellation is severe
+                if (threadIdx.x == 0) s_recompute = 0;
+                __syncthreads();
+                if (threadIdx.x < nb) {
+                    int tt = tix[threadIdx.x];
+                    double v1 = vn1[tt];
+                    if (v1 != 0.0) {
+                        double r = fabs(rowj[tt]) / v1;
+                        double q = 1.0 - r * r;
+                        q = q < 0.0 ? 0.0 : q;
+                        double ratio = v1 / vn2[tt];
+                        if (q * ratio * ratio <= tol3z) {
+                            atomicOr(&s_recompute, 1 << threadIdx.x);
+                        } else {
+                            vn1[tt] = v1 * sqrt(q);
+                        }
+                    }
+                }
+                __syncthreads();
+                int mask = s_recompute;
+                for (int b = 0; b < nb; ++b) {
+                    if (!(mask & (1 << b))) continue;
+                    double s = 0.0;
+                    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
+                        s = fma(cols[b][i], cols[b][i], s);
+                    s = block_sum(s, red);
+                    if (threadIdx.x == 0) {
+                        vn1[tix[b]] = sqrt(s);
+                        vn2[tix[b]] = vn1[tix[b]];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (!PIVOT && !g.sync()) return false;
+    if (prev_p >= 0 && prev_p % g.size == g.rank) {
+        double* cq = A + cm(0, prev_p, lda);
+        for (int i = n + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i];
+        if (threadIdx.x == 0) cq[n - 1] = prev_beta;
+    }
+    __syncthreads();
+    return true;
+}
+
+// C <- Q C (trans = false) or Q^T C (trans = true) for the rows 0..mrows-1 of the columns
+// [c0, c1) of C, where Q = H_0 H_1 ... H_{k-1} and H_j = I - tau[j] v_j v_j^T,
+// v_j = [0 (j entries); 1; Vr(j+1:mrows-1, j)]. Columns are independent, so any set of
+// CTAs can split them without synchronizing. If c_ident >= 0 the block [c0, c1) of C holds
+// columns c_ident.. of the identity, which H_j leaves untouched for j > column index:
+// those reflectors are skipped (valid for trans = false only, where H_{k-1} acts first).
+__device__ void apply_q_cols(bool trans, int mrows, int k, const double* Vr, int ldv,
+                             const double* tau, double* C, int ldc, int c0, int c1, int c_ident)
+{
+    __shared__ double red[kApplyBatch * 32];
+    for (int cb = c0; cb < c1; cb += kApplyBatch) {
+        int nb = min(kApplyBatch, c1 - cb);
+        double* cols[kApplyBatch];
+#pragma unroll
+        for (int b = 0; b < kApplyBatch; ++b) cols[b] = C + cm(0, cb + (b < nb ? b : 0), ldc);
+        int jmax = k - 1;
+        if (c_ident >= 0) jmax = min(jmax, c_ident + (cb - c0) + nb - 1);
+        for (int s = 0; s < k; ++s) {
+            int j = trans ? s : (k - 1 - s);
+            if (j > jmax) continue;
+            double tj = tau[j];
+            if (tj == 0.0) continue;
+            const double* v = Vr + cm(0, j, ldv);
+            double acc[kApplyBatch];
+#pragma unroll
+            for (int b = 0; b < kApplyBatch; ++b) acc[b] = 0.0;
+            for (int i = j + threadIdx.x; i < mrows; i += blockDim.x) {
+                double vi = (i == j) ? 1.0 : v[i];
+#pragma unroll
+                for (int b = 0; b < kApplyBatch; ++b)
+                    if (b < nb) acc[b] = fma(vi, cols[b][i], acc[b]);
+            }
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+            for (int b = 0; b < kApplyBatch; ++b) acc[b] = warp_sum(acc[b]);
+            __syncthreads();
+            if (lane == 0) {
+#pragma unroll
+                for (int b = 0; b < kApplyBatch; ++b) red[b * 32 + wid] = acc[b];
+            }
+            __syncthreads();
+            double w[kApplyBatch];
+#pragma unroll
+            for (int b = 0; b < kApplyBatch; ++b) {
+                double r = (lane < nw) ? red[b * 32 + lane] : 0.0;
+                w[b] = warp_sum(r) * tj;
+            }
+            for (int i = j + threadIdx.x; i < mrows; i += blockDim.x) {
+                double vi = (i == j) ? 1.0 : v[i];
+#pragma unroll
+                for (int b = 0; b < kApplyBatch; ++b)
+                    if (b < nb) cols[b][i] = fma(-w[b], vi, cols[b][i]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace mpj

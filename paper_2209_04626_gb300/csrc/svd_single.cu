@@ -1,0 +1,762 @@
+// svd_single.cu -- Algorithm 4 of the paper for one matrix, every stage spread over all
+// SMs. Stages (paper sections in brackets):
+//   [3.1] QRCP of A (optionally after a plain QR when m > n)      hh_qr<true>, persistent
+//   [3.5] special-case tests (cond_R, trailing norms, orth)        small kernels + FP32 GEMM
+//   [3.2] FP32 one-sided Jacobi on low(X), U only                   jacobi_sweeps<float>
+//   [3.3] switch: B = X^T U_low, B = Q R2, Y = X Q, V_acc = Q       GEMM, hh_qr<false>, GEMM
+//   [3.4] FP64 one-sided Jacobi on Y accumulating V_acc             jacobi_sweeps<double>
+//   [Alg. 1 end, Alg. 4 last line] Sigma, U_X, sort, U = Q [U_R; 0], V = P V_R
+// The branch decision stays on the device (gate_low); the kernels of the skipped stage
+// return immediately, so the whole call is asynchronous.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "gemm.cuh"
+#include "internal.h"
+#include "qr.cuh"
+#include "sweep.cuh"
+
+namespace mpj {
+
+constexpr int kWmaxLow = 16;   // template bound on the FP32 block width
+constexpr int kWmaxWork = 8;   // template bound on the FP64 block width
+constexpr int kThreadsLow = 512;
+constexpr int kThreadsWork = 256;
+constexpr int kQrThreads = 256;
+constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
+
+// True once the call cannot produce meaningful output: a non-finite input, or a
+// cooperative stage that gave up on a bounded wait. Later stages then return at once.
+__device__ __forceinline__ bool input_nonfinite(const DevState* st)
+{
+    return (*(volatile const int*)&st->status &
+            (MPJSVD_STATUS_NONFINITE | MPJSVD_STATUS_TIMEOUT)) != 0;
+}
+
+
+// ------------------------------------------------------------------------------------
+// elementwise / small kernels
+// ------------------------------------------------------------------------------------
+
+__global__ void k_copy_check(int m, int n, const double* __restrict__ A, int lda, double* W,
+                             int ldw, DevState* st)
+{
+    size_t total = (size_t)m * n;
+    int bad = 0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % m), j = (int)(e / m);
+        double v = A[cm(i, j, lda)];
+        if (!isfinite(v)) bad = 1;
+        W[cm(i, j, ldw)] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->status, MPJSVD_STATUS_NONFINITE);
+}
+
+// Wq(0:n-1, 0:n-1) = triu(W0(0:n-1, :)), zeros below (R1 of the plain QR).
+__global__ void k_extract_upper(int n, const double* __restrict__ W0, int ld0, double* Wq, int ldq)
+{
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        Wq[cm(i, j, ldq)] = (i <= j) ? W0[cm(i, j, ld0)] : 0.0;
+    }
+}
+
+// Logical order of the pivoted factorization: L(:, j) = W(:, perm[j]).
+__global__ void k_gather_cols(int m, int n, const double* __restrict__ W, int ldw, const int* perm,
+                              double* L, int ldl, const DevState* st)
+{
+    if (input_nonfinite(st)) return;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        int pj = perm[j];
+        if (pj < 0 || pj >= n) continue;  // only after a failed stage (status already set)
+        const double* src = W + cm(0, pj, ldw);
+        double* dst = L + cm(0, j, ldl);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// X = R^T (precond 0) or R (precond 1) from the upper triangle of L (n x n part).
+__global__ void k_form_x(int n, const double* __restrict__ L, int ldl, double* X, int precond)
+{
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        double v;
+        if (precond == MPJSVD_PRECOND_R) v = (i <= j) ? L[cm(i, j, ldl)] : 0.0;
+        else v = (i >= j) ? L[cm(j, i, ldl)] : 0.0;
+        X[cm(i, j, n)] = v;
+    }
+}
+
+// One warp per column: norms of an FP64 n-row matrix.
+__global__ void k_colnorms(int rows, int cols, const double* __restrict__ X, int ldx, double* out)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < cols; c += nw) {
+        const double* col = X + cm(0, c, ldx);
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s = fma(col[i], col[i], s);
+        s = warp_sum(s);
+        if (lane == 0) out[c] = sqrt(s);
+    }
+}
+
+// Section 3.5 tests that need no GEMM: cond_R and the trailing-norm test. Decides the branch
+// unless the orth test is still needed (branch = -1 then). One CTA.
+__global__ void k_branch_first(int n, const double* __restrict__ L, int ldl, const double* cn,
+                               int mode, double tol_cond_coef, double trailing_frac, DevState* st)
+{
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, cn[j]);
+    // block max
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
+        st->maxnorm = m2;
+        double r00 = fabs(L[cm(0, 0, ldl)]), rnn = fabs(L[cm(n - 1, n - 1, ldl)]);
+        double cond = (rnn > 0.0) ? r00 / rnn : INFINITY;
+        st->cond_r = cond;
+        int ntrail = (int)ceil(trailing_frac * (double)n);
+        int trailing_small = ntrail > 0;
+        const double sq_ulow = 2.44140625e-04;  // sqrt(2^-24)
+        for (int j = n - ntrail; j < n; ++j)
+            if (cn[j] > sq_ulow * m2) { trailing_small = 0; break; }
+        double tol_cond = tol_cond_coef * pow((double)n, 0.25);
+        int branch;
+        if (mode == MPJSVD_MODE_PLAIN) branch = 4;
+        else if (mode == MPJSVD_MODE_MIXED) branch = 0;
+        else if (cond <= tol_cond) branch = 1;
+        else if (trailing_small) branch = 2;
+        else branch = -1;  // orth test decides
+        st->branch = branch;
+        st->gate_low = (branch == 0) ? 1 : 0;
+        st->orth = -1.0;
+    }
+}
+
+// Xt = low(X) D^-1 with D the binary32 column norms of low(X). One warp per column.
+__global__ void k_scaled_low(int n, const double* __restrict__ X, float* Xt, const DevState* st)
+{
+    if (st->branch != -1) return;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < n; c += nw) {
+        const double* col = X + cm(0, c, n);
+        float s = 0.0f;
+        for (int i = lane; i < n; i += 32) {
+            float v = (float)col[i];
+            s = fmaf(v, v, s);
+        }
+        s = warp_sum(s);
+        float d = sqrtf(s);
+        for (int i = lane; i < n; i += 32) {
+            float v = (float)col[i];
+            Xt[cm(i, c, n)] = (d > 0.0f) ? v / d : 0.0f;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gemm(GemmArgs g, const int* gate, int gate_want)
+{
+    if (gate && *(volatile const int*)gate != gate_want) return;
+    int tiles_m = (g.M + kGemmBM - 1) / kGemmBM;
+    int tiles_n = (g.N + kGemmBN - 1) / kGemmBN;
+    for (int t = blockIdx.x; t < tiles_m * tiles_n; t += gridDim.x) {
+        int tm = t % tiles_m, tn = t / tiles_m;
+        gemm_tile<T>(g, tm * kGemmBM, tn * kGemmBN);
+    }
+}
+
+// orth = max |G - I| over the n x n FP32 Gram; atomicMax on the float bit pattern (>= 0).
+__global__ void k_orth_max(int n, const float* __restrict__ G, DevState* st, unsigned int* bits)
+{
+    if (st->branch != -1) return;
+    float mx = 0.0f;
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        float v = fabsf(G[e] - (i == j ? 1.0f : 0.0f));
+        mx = fmaxf(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits, __float_as_uint(mx));
+}
+
+__global__ void k_branch_final(DevState* st, const unsigned int* bits, double tol_orth)
+{
+    if (st->branch != -1) return;
+    float orth = __uint_as_float(*bits);
+    st->orth = orth;
+    st->branch = (orth <= tol_orth) ? 3 : 0;
+    st->gate_low = (st->branch == 0) ? 1 : 0;
+}
+
+__global__ void k_to_float(size_t count, const double* __restrict__ X, float* Xl, const DevState* st)
+{
+    if (!st->gate_low) return;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+         e += (size_t)gridDim.x * blockDim.x)
+        Xl[e] = (float)X[e];
+}
+
+// Descending stable rank sort of n keys: order[rank] = index. Grid-stride, O(n^2).
+template <typename T>
+__global__ void k_rank_desc(int n, const T* __restrict__ key, int* order, const DevState* st,
+                            int gate_want)
+{
+    if (gate_want >= 0 && st->gate_low != gate_want) return;
+    // keys are norms (>= 0); a NaN key is ordered below every number, so the ranks always
+    // form a permutation of 0..n-1
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        T kj = key[j];
+        kj = (kj == kj) ? kj : T(-1);
+        int r = 0;
+        for (int i = 0; i < n; ++i) {
+            T ki = key[i];
+            ki = (ki == ki) ? ki : T(-1);
+            r += (ki > kj) || (ki == kj && i < j);
+        }
+        order[r] = j;
+    }
+}
+
+template <typename T>
+__global__ void k_colnorms_gated(int rows, int cols, const T* __restrict__ X, int ldx, T* out,
+                                 const DevState* st)
+{
+    if (!st->gate_low) return;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < cols; c += nw) {
+        const T* col = X + cm(0, c, ldx);
+        T s = T(0);
+        for (int i = lane; i < rows; i += 32) s = fma(col[i], col[i], s);
+        s = warp_sum(s);
+        if (lane == 0) out[c] = sqrt(s);
+    }
+}
+
+// Ul(:, r) = double(Xl(:, order[r]) / sig[order[r]]) (normalized in binary32, Alg. 1 end).
+__global__ void k_make_ul(int n, const float* __restrict__ Xl, const float* sig, const int* order,
+                          double* Ul, const DevState* st)
+{
+    if (!st->gate_low) return;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        int j = order[r];
+        float s = sig[j];
+        const float* src = Xl + cm(0, j, n);
+        double* dst = Ul + cm(0, r, n);
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            dst[i] = (s > 0.0f) ? (double)(src[i] / s) : 0.0;
+    }
+}
+
+__global__ void k_identity(int n, double* Q, const DevState* st, int gate_want)
+{
+    if (gate_want >= 0 && st->gate_low != gate_want) return;
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        Q[e] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_copy_gated(size_t count, const double* __restrict__ src, double* dst,
+                             const DevState* st, int gate_want)
+{
+    if (st->gate_low != gate_want) return;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+         e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+// C <- Q C on columns split across CTAs (no grid synchronization needed).
+__global__ void k_apply_q(bool trans, int mrows, int ncols, int k, const double* Vr, int ldv,
+                          const double* tau, double* C, int ldc, int per_cta, int ident,
+                          const DevState* st, int gate_want)
+{
+    if (gate_want >= 0 && st->gate_low != gate_want) return;
+    int c0 = blockIdx.x * per_cta;
+    int c1 = min(ncols, c0 + per_cta);
+    if (c0 >= c1) return;
+    apply_q_cols(trans, mrows, k, Vr, ldv, tau, C, ldc, c0, c1, ident ? c0 : -1);
+}
+
+// ---- persistent cooperative kernels
+
+__global__ void k_hhqr_piv(int m, int n, double* W, int ldw, double* tau, int* perm, DevState* st)
+{
+    extern __shared__ double qr_dyn[];
+    if (input_nonfinite(st)) return;
+    Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    hh_qr<true>(g, m, n, W, ldw, tau, perm, qr_dyn);
+}
+
+__global__ void k_hhqr_plain(int m, int n, double* W, int ldw, double* tau, int* perm, DevState* st,
+                             int gate_want)
+{
+    extern __shared__ double qr_dyn[];
+    if (input_nonfinite(st)) return;
+    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
+    Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    hh_qr<false>(g, m, n, W, ldw, tau, perm, qr_dyn);
+}
+
+template <typename T, bool WITH_V, int WMAX>
+__global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, int gate_want)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (input_nonfinite(st)) return;
+    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
+    VisitSmem<T, WMAX> sm = carve_visit_smem<T, WMAX>(smem_raw, D.mX, D.w, WITH_V);
+    Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    bool conv = false;
+    int sweeps = jacobi_sweeps<T, WITH_V, WMAX>(g, D, X, V, st->rot_sweep[phase], sm, &conv);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps >= 0) {
+        unsigned long long tot = 0;
+        for (int s = 0; s < sweeps; ++s) tot += __ldcg(&st->rot_sweep[phase][s]);
+        if (phase == 0) { st->sweeps_low = sweeps; st->rot_low = tot; }
+        else { st->sweeps_work = sweeps; st->rot_work = tot; }
+        if (!conv) atomicOr(&st->status, MPJSVD_STATUS_NOT_CONVERGED);
+    }
+}
+
+// Final assembly (Alg. 1 end; Alg. 4 last line). One CTA per output column k:
+//   j = order[k]; S[k] = sig[j]; U_X(:, j) = Y(:, j) / sig[j];
+//   precond R^T: U_R = V_acc(:, j), V_R = U_X(:, j);  precond R: U_R = U_X(:, j), V_R = V_acc(:, j)
+//   V(jpvt[i], k) = s V_R(i, j); U(0:n-1, k) = s U_R(:, j); U(n:m-1, k) = 0,
+// with s = +-1 making the largest-magnitude entry of V(:, k) positive (lowest row on ties).
+__global__ void k_finalize(int m, int n, const double* __restrict__ Y, const double* __restrict__ Vacc,
+                           const double* sig, const int* order, const int* jpvt, int precond,
+                           double* U, double* S, double* V, DevState* st)
+{
+    __shared__ double s_val[32];
+    __shared__ int s_row[32];
+    __shared__ double s_sign;
+    if (input_nonfinite(st)) {  // outputs are not meaningful: make that visible
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int k = blockIdx.x; k < n; k += gridDim.x) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) U[cm(i, k, m)] = qnan;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) V[cm(i, k, n)] = qnan;
+            if (threadIdx.x == 0) S[k] = qnan;
+        }
+        return;
+    }
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        int j = order[k];
+        double sj = sig[j];
+        const double* y = Y + cm(0, j, n);
+        const double* va = Vacc + cm(0, j, n);
+        bool rt = (precond != MPJSVD_PRECOND_R);
+        // sign from V_R
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double vr = rt ? ((sj > 0.0) ? y[i] / sj : 0.0) : va[i];
+            double a = fabs(vr);
+            int row = jpvt[i];
+            if (a > bv || (a == bv && row < br)) { bv = a; br = row; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            int orow = __shfl_xor_sync(0xffffffffu, br, o);
+            if (ov > bv || (ov == bv && orow < br)) { bv = ov; br = orow; }
+        }
+        if ((threadIdx.x & 31) == 0) { s_val[threadIdx.x >> 5] = bv; s_row[threadIdx.x >> 5] = br; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b2 = -1.0;
+            int r2 = 0x7fffffff;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (s_val[w] > b2 || (s_val[w] == b2 && s_row[w] < r2)) { b2 = s_val[w]; r2 = s_row[w]; }
+            // find the signed value at row r2
+            s_sign = 1.0;
+            s_row[0] = r2;
+        }
+        __syncthreads();
+        int rbest = s_row[0];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            if (jpvt[i] == rbest) {
+                double vr = rt ? ((sj > 0.0) ? y[i] / sj : 0.0) : va[i];
+                s_sign = (vr < 0.0) ? -1.0 : 1.0;
+            }
+        }
+        __syncthreads();
+        double sg = s_sign;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double ux = (sj > 0.0) ? y[i] / sj : 0.0;
+            double uR = rt ? va[i] : ux;
+            double vR = rt ? ux : va[i];
+            U[cm(i, k, m)] = sg * uR;
+            V[cm(jpvt[i], k, n)] = sg * vR;
+        }
+        for (int i = n + threadIdx.x; i < m; i += blockDim.x) U[cm(i, k, m)] = 0.0;
+        if (threadIdx.x == 0) {
+            S[k] = sj;
+            if (sj == 0.0) atomicOr(&st->status, MPJSVD_STATUS_ZERO_SIGMA);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------
+
+static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct SingleLayout {
+    size_t off[24];
+    size_t total;
+};
+
+enum {
+    L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
+    L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_COUNT
+};
+
+static SingleLayout single_layout(int m, int n, bool qr_first)
+{
+    size_t nn = (size_t)n * n;
+    int mq = qr_first ? n : m;
+    size_t sz[L_COUNT] = {};
+    sz[L_WQ] = sizeof(double) * (size_t)mq * n;
+    sz[L_WQL] = sizeof(double) * (size_t)mq * n;
+    sz[L_W0] = qr_first ? sizeof(double) * (size_t)m * n : 0;
+    sz[L_TAU0] = sizeof(double) * n;
+    sz[L_TAU] = sizeof(double) * n;
+    sz[L_PERM] = sizeof(int) * n;
+    sz[L_IPOS] = sizeof(int) * n;
+    sz[L_VN1] = sizeof(double) * n;
+    sz[L_VN2] = sizeof(double) * n;
+    sz[L_X] = sizeof(double) * nn;
+    sz[L_XL] = sizeof(float) * nn;
+    sz[L_CN] = sizeof(double) * n;
+    sz[L_G] = sizeof(float) * nn;
+    sz[L_SIGL] = sizeof(float) * n;
+    sz[L_ORD] = sizeof(int) * n;
+    sz[L_UL] = sizeof(double) * nn;
+    sz[L_BQ] = sizeof(double) * nn;
+    sz[L_TAU2] = sizeof(double) * n;
+    sz[L_Y] = sizeof(double) * nn;
+    sz[L_VACC] = sizeof(double) * nn;
+    sz[L_SIG] = sizeof(double) * n;
+    sz[L_ORD2] = sizeof(int) * n;
+    sz[L_BITS] = 256;
+    sz[L_PERM2] = sizeof(int) * n;
+    SingleLayout L;
+    size_t o = 0;
+    for (int i = 0; i < L_COUNT; ++i) {
+        L.off[i] = o;
+        o += align256(sz[i] ? sz[i] : 16);
+    }
+    L.total = o;
+    return L;
+}
+
+static int even_ceil(int x) { return x <= 1 ? 1 : ((x + 1) & ~1); }
+
+// Block width of the sweeps. FP64 (work): just enough blocks to give every SM a visit per
+// round (the stage is FP64-throughput bound), capped by shared memory. FP32 (low): wide
+// blocks (the stage is latency bound: fewer rounds, fewer barriers).
+static int pick_w(int n, int mX, bool low, int sms, int forced)
+{
+    int wmax = low ? kWmaxLow : kWmaxWork;
+    int elem = low ? 4 : 8;
+    int smem_cap = (int)((150 * 1024) / ((size_t)2 * mX * elem));
+    int w;
+    if (forced > 0) {
+        w = forced;
+    } else if (low) {
+        w = 16;
+    } else {
+        w = even_ceil((n + 2 * sms - 1) / (2 * sms));
+        if (n <= 512) w = std::max(w, 8);
+    }
+    w = std::min(w, std::min(wmax, smem_cap));
+    w = std::min(w, std::max(1, n / 2));
+    if (w > 1 && (w & 1)) w -= 1;
+    return std::max(w, 1);
+}
+
+template <typename T, bool WITH_V, int WMAX>
+static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
+                         double tol, DevState* st, int phase, int gate_want, int threads)
+{
+    SweepDims D;
+    D.n = n;
+    D.mX = mX;
+    D.ldX = mX;
+    D.nV = WITH_V ? n : 0;
+    D.ldV = n;
+    D.w = w;
+    int nb = (n + w - 1) / w;
+    D.k = nb + (nb & 1);
+    if (D.k < 2) D.k = 2;
+    D.maxsweep = std::min(maxsweep, 64);
+    D.tol = tol;
+    size_t smem = sweep_smem_bytes<T, WMAX>(mX, w, WITH_V);
+    auto kern = k_sweeps<T, WITH_V, WMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("sweep smem attribute", e);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_fail("sweep occupancy", e);
+    if (occ < 1) return cuda_fail("sweep occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
+    int grid = std::min(D.k / 2, occ * h->num_sms);
+    grid = std::min(grid, 1024);
+    void* args[] = {&D, &X, &V, &st, &phase, &gate_want};
+    e = cudaLaunchCooperativeKernel((void*)kern, grid, threads, args, smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail("sweep launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+static int launch_hhqr(mpjsvd_ctx* h, bool pivot, int m, int n, double* W, int ldw, double* tau,
+                       int* perm, DevState* st, int gate_want)
+{
+    int grid = std::max(1, std::min(n, std::min(h->num_sms, kMaxGroupCtas)));
+    size_t smem = hh_qr_smem_bytes(m, n, grid);
+    if (smem > 200 * 1024) return cuda_fail("hh_qr: too many rows", cudaErrorInvalidValue);
+    void* kern = pivot ? (void*)k_hhqr_piv : (void*)k_hhqr_plain;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("hhqr smem attribute", e);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kQrThreads, smem);
+    if (e != cudaSuccess) return cuda_fail("hhqr occupancy", e);
+    if (occ < 1) return cuda_fail("hhqr occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
+    if (pivot) {
+        void* args[] = {&m, &n, &W, &ldw, &tau, &perm, &st};
+        e = cudaLaunchCooperativeKernel(kern, grid, kQrThreads, args, smem, h->stream);
+    } else {
+        void* args[] = {&m, &n, &W, &ldw, &tau, &perm, &st, &gate_want};
+        e = cudaLaunchCooperativeKernel(kern, grid, kQrThreads, args, smem, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail("hhqr launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+static int launch_apply_q(mpjsvd_ctx* h, int mrows, int ncols, int k, const double* Vr, int ldv,
+                          const double* tau, double* C, int ldc, bool ident, DevState* st,
+                          int gate_want)
+{
+    int per = std::max(1, (ncols + h->num_sms - 1) / h->num_sms);
+    int grid = (ncols + per - 1) / per;
+    k_apply_q<<<grid, 256, 0, h->stream>>>(false, mrows, ncols, k, Vr, ldv, tau, C, ldc, per,
+                                           ident ? 1 : 0, st, gate_want);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("apply_q launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+static int launch_gemm_d(mpjsvd_ctx* h, const GemmArgs& g, const int* gate, int want)
+{
+    int tiles = ((g.M + kGemmBM - 1) / kGemmBM) * ((g.N + kGemmBN - 1) / kGemmBN);
+    k_gemm<double><<<tiles, kGemmThreads, 0, h->stream>>>(g, gate, want); ++h->launch_count;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("gemm launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+static void record(mpjsvd_ctx* h, int i)
+{
+    if (h->params.timing && h->have_events) cudaEventRecord(h->ev[i], h->stream);
+}
+
+int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U, double* S,
+               double* V, double tol)
+{
+    const mpjsvd_params& P = h->params;
+    const bool qr_first = P.qr_first && m > n;
+    SingleLayout L = single_layout(m, n, qr_first);
+    int rc = ensure_buffer(&h->ws, &h->ws_bytes, L.total);
+    if (rc) return rc;
+    char* base = (char*)h->ws;
+    auto ptr = [&](int i) { return (void*)(base + L.off[i]); };
+    double* Wq = (double*)ptr(L_WQ);
+    double* WqL = (double*)ptr(L_WQL);
+    double* W0 = (double*)ptr(L_W0);
+    double* tau0 = (double*)ptr(L_TAU0);
+    double* tau = (double*)ptr(L_TAU);
+    int* perm = (int*)ptr(L_PERM);
+    double* X = (double*)ptr(L_X);
+    float* Xl = (float*)ptr(L_XL);
+    double* cn = (double*)ptr(L_CN);
+    float* G = (float*)ptr(L_G);
+    float* sigl = (float*)ptr(L_SIGL);
+    int* ord = (int*)ptr(L_ORD);
+    double* Ul = (double*)ptr(L_UL);
+    double* Bq = (double*)ptr(L_BQ);
+    double* tau2 = (double*)ptr(L_TAU2);
+    double* Y = (double*)ptr(L_Y);
+    double* Vacc = (double*)ptr(L_VACC);
+    double* sig = (double*)ptr(L_SIG);
+    int* ord2 = (int*)ptr(L_ORD2);
+    unsigned int* bits = (unsigned int*)ptr(L_BITS);
+    int* perm2 = (int*)ptr(L_PERM2);
+    DevState* st = (DevState*)h->dstate;
+    cudaStream_t s = h->stream;
+    const int T256 = 256;
+    const int egrid = h->num_sms * 4;
+    const int mq = qr_first ? n : m;
+    cudaError_t e;
+    h->launch_count = 0;
+
+    e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    if (e != cudaSuccess) return cuda_fail("memset state", e);
+    e = cudaMemsetAsync(bits, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail("memset bits", e);
+    record(h, 0);
+
+    // ---- [3.1] QR preconditioning
+    if (qr_first) {
+        k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, W0, m, st); ++h->launch_count;
+        if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1))) return rc;
+        k_extract_upper<<<egrid, T256, 0, s>>>(n, W0, m, Wq, n); ++h->launch_count;
+    } else {
+        k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, Wq, m, st); ++h->launch_count;
+    }
+    if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1))) return rc;
+    k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
+    k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, X, P.precond); ++h->launch_count;
+    record(h, 1);
+
+    // ---- [3.5] special cases
+    k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, X, n, cn); ++h->launch_count;
+    k_branch_first<<<1, 1024, 0, s>>>(n, WqL, mq, cn, P.mode, P.tol_cond_coef, P.trailing_frac, st); ++h->launch_count;
+    if (P.mode == MPJSVD_MODE_AUTO) {
+        k_scaled_low<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, X, Xl, st); ++h->launch_count;
+        GemmArgs g;
+        g.M = n; g.N = n; g.K = n;
+        g.A = Xl; g.lda = n; g.transA = true;
+        g.B = Xl; g.ldb = n; g.C = G; g.ldc = n;
+        // Xt^T Xt: X = R^T (lower) -> Xt(i, a) = 0 for i < a; X = R (upper) -> 0 for i > a
+        g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);
+        g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
+        int tiles = ((n + kGemmBM - 1) / kGemmBM) * ((n + kGemmBN - 1) / kGemmBN);
+        // gate on branch == -1 is checked inside k_orth_max/k_branch_final; the Gram runs
+        // unconditionally in auto mode (one FP32 GEMM, cheap)
+        k_gemm<float><<<tiles, kGemmThreads, 0, s>>>(g, nullptr, 0); ++h->launch_count;
+        k_orth_max<<<egrid, T256, 0, s>>>(n, G, st, bits); ++h->launch_count;
+        k_branch_final<<<1, 1, 0, s>>>(st, bits, P.tol_orth); ++h->launch_count;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("branch kernels", e);
+    record(h, 2);
+
+    // ---- [3.2] binary32 Jacobi on low(X), U only (gated)
+    const size_t nn = (size_t)n * n;
+    int w_low = pick_w(n, n, true, h->num_sms, P.block_w);
+    int w_work = pick_w(n, n, false, h->num_sms, P.block_w);
+    h->last_block_w_low = (P.mode == MPJSVD_MODE_PLAIN) ? 0 : w_low;
+    h->last_block_w_work = w_work;
+    if (P.mode != MPJSVD_MODE_PLAIN) {
+        k_to_float<<<egrid, T256, 0, s>>>(nn, X, Xl, st); ++h->launch_count;
+        const double tol_low = std::sqrt((double)n) * 5.9604644775390625e-08;
+        if ((rc = launch_sweeps<float, false, kWmaxLow>(h, n, n, Xl, nullptr, w_low, P.maxsweep,
+                                                        tol_low, st, 0, 1, kThreadsLow)))
+            return rc;
+        k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
+        k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
+        k_make_ul<<<std::min(n, egrid), T256, 0, s>>>(n, Xl, sigl, ord, Ul, st); ++h->launch_count;
+        record(h, 3);
+        // ---- [3.3] switch: B = X^T U_low; B = Q R2; V_acc = Q; Y = X Q
+        GemmArgs g;
+        g.M = n; g.N = n; g.K = n;
+        g.A = X; g.lda = n; g.transA = true;
+        g.B = Ul; g.ldb = n; g.C = Bq; g.ldc = n;
+        g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);  // X^T upper when X lower
+        g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
+        if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
+        if ((rc = launch_hhqr(h, false, n, n, Bq, n, tau2, perm2, st, 1))) return rc;
+        k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
+        if ((rc = launch_apply_q(h, n, n, n, Bq, n, tau2, Vacc, n, true, st, 1))) return rc;
+        GemmArgs g2;
+        g2.M = n; g2.N = n; g2.K = n;
+        g2.A = X; g2.lda = n; g2.transA = false;
+        g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
+        g2.klo_from_row = (P.precond == MPJSVD_PRECOND_R);  // X upper: X(i, k) = 0 for k < i
+        g2.khi_from_row = (P.precond != MPJSVD_PRECOND_R);  // X lower: X(i, k) = 0 for k > i
+        if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
+    } else {
+        record(h, 3);
+    }
+    // skipped low stage: Y = X, V_acc = I
+    k_copy_gated<<<egrid, T256, 0, s>>>(nn, X, Y, st, 0); ++h->launch_count;
+    k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 0); ++h->launch_count;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("switch kernels", e);
+    record(h, 4);
+
+    // ---- [3.4] binary64 refinement with V accumulation
+    const double tol_work = (tol > 0.0) ? tol : std::sqrt((double)n) * 1.1102230246251565e-16;
+    if ((rc = launch_sweeps<double, true, kWmaxWork>(h, n, n, Y, Vacc, w_work, P.maxsweep, tol_work,
+                                                     st, 1, -1, kThreadsWork)))
+        return rc;
+    record(h, 5);
+
+    // ---- Sigma, U_X, sort, U = Q [U_R; 0], V = P V_R
+    k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Y, n, sig); ++h->launch_count;
+    k_rank_desc<double><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sig, ord2, st, -1); ++h->launch_count;
+    k_finalize<<<std::min(n, egrid), T256, 0, s>>>(m, n, Y, Vacc, sig, ord2, perm, P.precond, U, S, V, st); ++h->launch_count;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("finalize kernels", e);
+    if (qr_first) {
+        if ((rc = launch_apply_q(h, n, n, n, WqL, n, tau, U, m, false, st, -1))) return rc;
+        if ((rc = launch_apply_q(h, m, n, n, W0, m, tau0, U, m, false, st, -1))) return rc;
+    } else {
+        if ((rc = launch_apply_q(h, m, n, n, WqL, m, tau, U, m, false, st, -1))) return rc;
+    }
+    record(h, 6);
+    return 0;
+}
+
+int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
+{
+    DevState st;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail("stream sync", e);
+    e = cudaMemcpy(&st, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("stats copy", e);
+    mpjsvd_stats r;
+    memset(&r, 0, sizeof(r));
+    r.status = st.status;
+    r.branch = st.branch;
+    r.sweeps_low = st.sweeps_low;
+    r.sweeps_work = st.sweeps_work;
+    r.rot_low = (long long)st.rot_low;
+    r.rot_work = (long long)st.rot_work;
+    r.cond_r = st.cond_r;
+    r.orth = st.orth;
+    r.block_w_low = st.branch == 0 ? h->last_block_w_low : 0;
+    r.block_w_work = h->last_block_w_work;
+    r.launches = h->launch_count;
+    if (h->params.timing && h->have_events) {
+        float* t[6] = {&r.ms_qr, &r.ms_branch, &r.ms_low, &r.ms_switch, &r.ms_work, &r.ms_final};
+        for (int i = 0; i < 6; ++i) cudaEventElapsedTime(t[i], h->ev[i], h->ev[i + 1]);
+    }
+    *out = r;
+    return 0;
+}
+
+}  // namespace mpj

@@ -1,0 +1,278 @@
+"""Thin Python binding of libmpjsvd (include/mpjsvd.h).
+
+Argument marshalling only: every step of the SVD runs in the library's CUDA kernels.
+PyTorch provides device memory and the stream. The functions named ``mpjsvd_*`` mirror
+the C entry points one to one; ``svd`` / ``svd_batched`` / ``SVDFunction`` are
+conveniences built on them.
+
+Layout: the library works on column-major FP64 matrices. A column-major m x n matrix is
+held here as a torch tensor of shape (m, n) with strides (1, m) (``colmajor`` makes one).
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmpjsvd.so")
+
+MODE = {"auto": 0, "mixed": 1, "plain": 2}
+PRECOND = {"rt": 0, "r": 1}
+BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
+STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
+
+EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsvd_set_params",
+           "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
+           "mpjsvd_destroy", "mpjsvd_last_error"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tol_alg", ctypes.c_double), ("tol_orth", ctypes.c_double),
+                ("tol_cond_coef", ctypes.c_double), ("trailing_frac", ctypes.c_double),
+                ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
+                ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
+                ("sweeps_work", ctypes.c_int), ("rot_low", ctypes.c_longlong),
+                ("rot_work", ctypes.c_longlong), ("cond_r", ctypes.c_double),
+                ("orth", ctypes.c_double), ("block_w_low", ctypes.c_int),
+                ("block_w_work", ctypes.c_int), ("ms_qr", ctypes.c_float),
+                ("ms_branch", ctypes.c_float), ("ms_low", ctypes.c_float),
+                ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
+                ("ms_final", ctypes.c_float), ("launches", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["branch_name"] = BRANCH.get(d["branch"], "?")
+        return d
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+def load_library(path=LIB_PATH):
+    """Load libmpjsvd.so. Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libmpjsvd.so not found at %s: run __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)" % path)
+    L = ctypes.CDLL(path)
+    L.mpjsvd_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.mpjsvd_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp]
+    L.mpjsvd_set_stream.argtypes = [_vp, _vp]
+    L.mpjsvd_set_params.argtypes = [_vp, ctypes.POINTER(Params)]
+    L.mpjsvd_svd.argtypes = [_vp, _i, _i, _vp, _i, _vp, _vp, _vp, _d]
+    L.mpjsvd_svd_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp]
+    L.mpjsvd_svd_backward.argtypes = [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d,
+                                      ctypes.POINTER(_i)]
+    L.mpjsvd_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+    L.mpjsvd_destroy.argtypes = [_vp]
+    L.mpjsvd_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------- C entry points, 1:1
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError("%s failed with %d (%s)" % (what, rc,
+                                                        load_library().mpjsvd_last_error().decode()))
+
+
+def mpjsvd_default_params(**overrides):
+    p = Params()
+    load_library().mpjsvd_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "mode" and isinstance(v, str):
+            v = MODE[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
+        setattr(p, k, v)
+    return p
+
+
+def mpjsvd_create(params=None, stream=None):
+    h = _vp()
+    s = _vp(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(load_library().mpjsvd_create(ctypes.byref(h), ctypes.byref(params) if params else None, s),
+           "mpjsvd_create")
+    return h
+
+
+def mpjsvd_set_stream(h, stream):
+    _check(load_library().mpjsvd_set_stream(h, _vp(stream)), "mpjsvd_set_stream")
+
+
+def mpjsvd_set_params(h, params):
+    _check(load_library().mpjsvd_set_params(h, ctypes.byref(params)), "mpjsvd_set_params")
+
+
+def mpjsvd_svd(h, m, n, A_ptr, lda, U_ptr, S_ptr, V_ptr, tol=0.0):
+    return load_library().mpjsvd_svd(h, m, n, _vp(A_ptr), lda, _vp(U_ptr), _vp(S_ptr), _vp(V_ptr), tol)
+
+
+def mpjsvd_svd_batched(h, batch, m_host, n_host, lda_host, A_ptrs, U_ptrs, S_ptrs, V_ptrs, tol, info_ptr):
+    return load_library().mpjsvd_svd_batched(h, batch, _vp(m_host), _vp(n_host), _vp(lda_host),
+                                             _vp(A_ptrs), _vp(U_ptrs), _vp(S_ptrs), _vp(V_ptrs), tol,
+                                             _vp(info_ptr))
+
+
+def mpjsvd_svd_backward(h, m, n, U_ptr, S_ptr, V_ptr, gU_ptr, gS_ptr, gV_ptr, gA_ptr, gap_tol=1e-3):
+    nf = _i(0)
+    rc = load_library().mpjsvd_svd_backward(h, m, n, _vp(U_ptr), _vp(S_ptr), _vp(V_ptr),
+                                            _vp(gU_ptr), _vp(gS_ptr), _vp(gV_ptr), _vp(gA_ptr),
+                                            gap_tol, ctypes.byref(nf))
+    return rc, nf.value
+
+
+def mpjsvd_get_stats(h):
+    st = Stats()
+    _check(load_library().mpjsvd_get_stats(h, ctypes.byref(st)), "mpjsvd_get_stats")
+    return st.as_dict()
+
+
+def mpjsvd_destroy(h):
+    if h:
+        load_library().mpjsvd_destroy(h)
+
+
+def mpjsvd_last_error():
+    return load_library().mpjsvd_last_error().decode()
+
+
+# ---------------------------------------------------------------- conveniences
+
+def colmajor(x, device=None):
+    """A (m, n) float64 tensor with column-major strides (1, m), holding x's values."""
+    x = torch.as_tensor(x, dtype=torch.float64)
+    m, n = x.shape
+    out = torch.empty((n, m), dtype=torch.float64, device=device or x.device).t()
+    out.copy_(x)
+    return out
+
+
+def empty_colmajor(m, n, device):
+    return torch.empty((n, m), dtype=torch.float64, device=device).t()
+
+
+def _is_colmajor(x):
+    return x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0])
+
+
+class Handle:
+    """Owns an mpjsvd handle bound to the current CUDA device and stream."""
+
+    def __init__(self, **params):
+        self.params = mpjsvd_default_params(**params)
+        self.h = mpjsvd_create(self.params)
+
+    def set(self, **params):
+        for k, v in params.items():
+            if k == "mode" and isinstance(v, str):
+                v = MODE[v]
+            if k == "precond" and isinstance(v, str):
+                v = PRECOND[v]
+            setattr(self.params, k, v)
+        mpjsvd_set_params(self.h, self.params)
+
+    def svd(self, A, tol=0.0, out=None):
+        """Thin SVD of a CUDA float64 column-major (m, n) tensor. Returns (U, S, V)."""
+        if not (A.is_cuda and A.dtype == torch.float64):
+            raise TypeError("A must be a CUDA float64 tensor")
+        if not _is_colmajor(A):
+            A = colmajor(A, A.device)
+        m, n = A.shape
+        if out is None:
+            U = empty_colmajor(m, n, A.device)
+            S = torch.empty(n, dtype=torch.float64, device=A.device)
+            V = empty_colmajor(n, n, A.device)
+        else:
+            U, S, V = out
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(A.device).cuda_stream)
+        rc = mpjsvd_svd(self.h, m, n, A.data_ptr(), A.stride(1), U.data_ptr(), S.data_ptr(),
+                        V.data_ptr(), tol)
+        _check(rc, "mpjsvd_svd")
+        return U, S, V
+
+    def stats(self):
+        return mpjsvd_get_stats(self.h)
+
+    def backward(self, U, S, V, gU=None, gS=None, gV=None, gap_tol=1e-3):
+        m, n = U.shape
+        gA = empty_colmajor(m, n, U.device)
+        cm = lambda t: (colmajor(t, U.device) if t.dim() == 2 and not _is_colmajor(t) else t)
+        gU = cm(gU) if gU is not None else None
+        gV = cm(gV) if gV is not None else None
+        gS = gS.contiguous() if gS is not None else None
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(U.device).cuda_stream)
+        rc, nf = mpjsvd_svd_backward(self.h, m, n, U.data_ptr(), S.data_ptr(), V.data_ptr(),
+                                     gU.data_ptr() if gU is not None else None,
+                                     gS.data_ptr() if gS is not None else None,
+                                     gV.data_ptr() if gV is not None else None,
+                                     gA.data_ptr(), gap_tol)
+        _check(rc, "mpjsvd_svd_backward")
+        return gA, nf
+
+    def close(self):
+        if self.h:
+            mpjsvd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default = {}
+
+
+def default_handle(device=None):
+    dev = torch.cuda.current_device() if device is None else device
+    if dev not in _default:
+        with torch.cuda.device(dev):
+            _default[dev] = Handle()
+    return _default[dev]
+
+
+def svd(A, mode="auto", tol=0.0, **params):
+    """Thin SVD through the library. A CPU input is copied to the current GPU and the
+    factors are copied back (end-to-end use); a CUDA input stays on the device."""
+    host = not A.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Ad = colmajor(A.to(torch.float64), dev) if host else A
+    h = default_handle(Ad.device.index)
+    h.set(mode=mode, **params)
+    U, S, V = h.svd(Ad, tol=tol)
+    if host:
+        return U.cpu(), S.cpu(), V.cpu()
+    return U, S, V
+
+
+class SVDFunction(torch.autograd.Function):
+    """A -> (U, S, V) with the library's forward and hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, A, mode="auto"):
+        h = default_handle(A.device.index)
+        h.set(mode=mode)
+        U, S, V = h.svd(A.detach())
+        ctx.save_for_backward(U, S, V)
+        return U, S, V
+
+    @staticmethod
+    def backward(ctx, gU, gS, gV):
+        U, S, V = ctx.saved_tensors
+        h = default_handle(U.device.index)
+        gA, nf = h.backward(U, S, V, gU, gS, gV)
+        ctx.n_flagged = nf
+        return gA, None

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/mpjsvd.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "mpjsvd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpjsvd_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2209_04626_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["mpjsvd_create", "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward",
+                     "mpjsvd_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_2209_04626_gb300 import mpjsvd
+    assert sorted(mpjsvd.EXPORTS) == _declared()
+    for name in _declared():
+        assert callable(getattr(mpjsvd, name))
+
+
+def test_struct_sizes_match_header(lib_path):
+    """The ctypes mirrors of mpjsvd_params / mpjsvd_stats have the C layout."""
+    from paper_2209_04626_gb300 import mpjsvd
+    # 4 doubles + 6 ints
+    assert ctypes.sizeof(mpjsvd.Params) == 4 * 8 + 6 * 4
+    # 4 ints, 2 long long, 2 doubles, 2 ints, 6 floats, 1 int, padded to 8 bytes
+    raw = 4 * 4 + 2 * 8 + 2 * 8 + 2 * 4 + 6 * 4 + 4
+    assert ctypes.sizeof(mpjsvd.Stats) == (raw + 7) // 8 * 8
+
+
+def test_default_params_are_the_papers(lib_path):
+    from paper_2209_04626_gb300 import mpjsvd
+    p = mpjsvd.mpjsvd_default_params()
+    assert (p.tol_alg, p.tol_orth, p.tol_cond_coef) == (1e-2, 1e-5, 1.5)
+    assert p.maxsweep == 30 and p.mode == 0
+
+
+def test_argument_validation_without_gpu(lib_path):
+    """Invalid arguments are rejected before any CUDA call (LAPACK-style -i codes)."""
+    lib = ctypes.CDLL(lib_path)
+    f = lib.mpjsvd_svd
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]
+    assert f(None, 4, 2, None, 4, None, None, None, 0.0) == -1
+    lib.mpjsvd_default_params.argtypes = [ctypes.c_void_p]
+    assert lib.mpjsvd_default_params(None) == -1

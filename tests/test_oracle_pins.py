@@ -328,3 +328,35 @@ def test_adjoint_flags_near_degenerate():
     U, S, V, _ = oracle.svd(A)
     _, nf = oracle.svd_backward(U, S, V, gS=np.ones(4), gap_tol=1e-6)
     assert nf == 1
+
+
+# ---------------------------------------------------------------- extended-precision build
+
+def test_extended_oracle_against_mpmath():
+    """The long double build of the same oracle is the extended reference; pin it to
+    mpmath at 40 digits (its error must be far below binary64's)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(26)
+    A = inputs.known_sigma(rng, 7, 5, np.logspace(0, -6, 5))
+    _, Se, _, st = oracle.svd(A, mode="plain", ext=True)
+    _, Sd, _, _ = oracle.svd(A, mode="plain")
+    s_hp = sorted(mpmath.svd_r(mpmath.matrix(A.tolist()), compute_uv=False), reverse=True)
+    rel_e = max(float(abs(mpmath.mpf(str(se)) - sh) / sh) for se, sh in zip(Se, s_hp))
+    rel_d = max(float(abs(mpmath.mpf(float(sd)) - sh) / sh) for sd, sh in zip(Sd, s_hp))
+    # relative perturbation bound of Jacobi: O(u kappa(B_c)), B_c = A with unit columns
+    kappa_bc = np.linalg.cond(A / np.linalg.norm(A, axis=0))
+    assert rel_e <= 64 * oracle.unit_roundoff(ext=True) * kappa_bc
+    assert rel_d <= 64 * 2.0 ** -53 * kappa_bc
+    assert rel_e * 100 < rel_d  # the extended build really is the more accurate reference
+
+
+def test_binary64_oracle_error_is_attributed_to_precision():
+    """On a column-scaled condition ~1e6 input, the binary64 oracle differs from the
+    extended build by more than binary64 rounding of sigma but far below u * kappa."""
+    A, _ = inputs.plain_256x128(m=64, n=32)
+    _, S, _, _ = oracle.svd(A, mode="plain")
+    _, Se, _, _ = oracle.svd(A, mode="plain", ext=True)
+    e = float(np.max(np.abs(np.asarray(S, dtype=np.longdouble) - Se) / Se))
+    Bc = A / np.linalg.norm(A, axis=0)
+    assert e < 2.0 ** -53 * np.linalg.cond(Bc) * 64
