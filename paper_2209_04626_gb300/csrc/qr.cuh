@@ -18,11 +18,14 @@ constexpr int kQrColBatch = 4;     // owned columns reduced together per pass
 constexpr int kQrSlotStride = 256; // pivot-candidate slots per step parity (max CTAs)
 constexpr int kApplyBatch = 8;     // columns of C updated per pass of apply_q_cols
 
-// Householder vector of x = A(j:m-1, p) into vs[j..m-1] (vs[j] = 1), returns tau and beta.
-// H = I - tau v v^T, H x = beta e_1, beta = -sign(x_0) |x|. The tail is divided (not
-// multiplied by a reciprocal) by x_0 - beta.
+// Householder reflector of x = A(j:m-1, p) (Section 3.1): H = I - tau v v^T with
+// v = [1; x(1:) * rden], rden = 1 / (x_0 - beta), beta = -sign(x_0) |x|, H x = beta e_1.
+// vs[j+1..m-1] receives the UNSCALED tail x(1:); the scale rden is applied to the two
+// scalars of each column update instead of to every element (an FP64 division or
+// multiply per element would be repeated by every CTA).
 __device__ __forceinline__ void house_vector(int m, int j, const double* __restrict__ col,
-                                             double* vs, double* red, double& tau, double& beta)
+                                             double* vs, double* red, double& tau, double& beta,
+                                             double& rden)
 {
     // the pivot column was last written by its owner CTA: read through L2 (__ldcg), never
     // from a possibly stale L1 line
@@ -37,45 +40,35 @@ __device__ __forceinline__ void house_vector(int m, int j, const double* __restr
     if (s == 0.0) {
         tau = 0.0;
         beta = alpha;
+        rden = 0.0;
     } else {
         double nrm = sqrt(fma(alpha, alpha, s));
         beta = (alpha >= 0.0) ? -nrm : nrm;
         tau = (beta - alpha) / beta;
-        double den = alpha - beta;
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) vs[i] = vs[i] / den;
+        rden = 1.0 / (alpha - beta);
     }
-    if (threadIdx.x == 0) vs[j] = 1.0;
     __syncthreads();
 }
 
-// Partial dot products of v (rows j..m-1) with up to kQrColBatch columns, reduced over the
-// CTA. red must hold >= kQrColBatch * 32 doubles. Result in w[] (all threads).
+// Partial dot products of the unscaled tail (rows j+1..m-1) with up to kQrColBatch
+// columns, reduced over the CTA. red must hold >= kQrColBatch * 32 doubles. Result in w[]
+// (all threads).
 __device__ __forceinline__ void batch_dots(int m, int j, const double* vs, double* const* cols,
                                            int nb, double* red, double* w)
 {
     double acc[kQrColBatch];
 #pragma unroll
     for (int b = 0; b < kQrColBatch; ++b) acc[b] = 0.0;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
         double vi = vs[i];
 #pragma unroll
         for (int b = 0; b < kQrColBatch; ++b)
             if (b < nb) acc[b] = fma(vi, cols[b][i], acc[b]);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double out[kQrColBatch];
+    block_sum_multi<kQrColBatch>(acc, red, out);
 #pragma unroll
-    for (int b = 0; b < kQrColBatch; ++b) acc[b] = warp_sum(acc[b]);
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int b = 0; b < kQrColBatch; ++b) red[b * 32 + wid] = acc[b];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < kQrColBatch; ++b) {
-        double r = (lane < nw) ? red[b * 32 + lane] : 0.0;
-        w[b] = warp_sum(r);
-    }
+    for (int b = 0; b < kQrColBatch; ++b) w[b] = out[b];
 }
 
 // Column-distributed Householder QR (PIVOT = false) or QR with column pivoting
@@ -96,7 +89,7 @@ template <bool PIVOT>
 __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* tau, int* perm,
                       double* smem)
 {
-    __shared__ double red[kQrColBatch * 32];
+    __shared__ double red[kQrColBatch * 33];
     __shared__ int s_piv;
     __shared__ int s_recompute;
     const double tol3z = 1.0536712127723509e-08;  // sqrt(2^-53)
@@ -126,7 +119,7 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
     __syncthreads();
 
     int prev_p = -1;       // pivot column of the previous step (its store is deferred)
-    double prev_beta = 0.0;
+    double prev_beta = 0.0, prev_rden = 0.0;
     for (int j = 0; j < n; ++j) {
         // ---- pivot column of this step
         if (PIVOT) {
@@ -185,14 +178,14 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
         //      every CTA reads the pivot column during its own step
         if (prev_p >= 0 && prev_p % g.size == g.rank) {
             double* cq = A + cm(0, prev_p, lda);
-            for (int i = j + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i];
+            for (int i = j + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i] * prev_rden;
             if (threadIdx.x == 0) cq[j - 1] = prev_beta;
         }
         __syncthreads();
 
         // ---- Householder vector, computed redundantly by every CTA
-        double tj, beta;
-        house_vector(m, j, colp, vs, red, tj, beta);
+        double tj, beta, rden;
+        house_vector(m, j, colp, vs, red, tj, beta, rden);
 
         if (p % g.size == g.rank) {
             if (threadIdx.x == 0) {
@@ -203,6 +196,7 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
         }
         prev_p = p;
         prev_beta = beta;
+        prev_rden = rden;
         __syncthreads();
 
         // ---- apply H_j to this CTA's active columns, kQrColBatch at a time
@@ -223,17 +217,27 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
             if (nb == 0) break;
             for (int b = nb; b < kQrColBatch; ++b) { cols[b] = cols[0]; tix[b] = tix[0]; }
             if (tj != 0.0) {
-                double w[kQrColBatch];
+                // w = tau (c_j + rden x^T c_tail); c_j -= w; c_tail -= (w rden) x
+                double w[kQrColBatch], f[kQrColBatch];
                 batch_dots(m, j, vs, cols, nb, red, w);
-                for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
-                    double vi = vs[i];
+#pragma unroll
+                for (int b = 0; b < kQrColBatch; ++b) {
+                    w[b] = tj * fma(rden, w[b], cols[b][j]);
+                    f[b] = w[b] * rden;
+                }
+                __syncthreads();  // every thread has read c_j before it changes
+                if (threadIdx.x == 0) {
+                    for (int b = 0; b < nb; ++b) {
+                        double nv = cols[b][j] - w[b];
+                        cols[b][j] = nv;
+                        if (PIVOT) rowj[tix[b]] = nv;
+                    }
+                }
+                for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+                    double xi = vs[i];
 #pragma unroll
                     for (int b = 0; b < kQrColBatch; ++b)
-                        if (b < nb) {
-                            double nv = fma(-tj * w[b], vi, cols[b][i]);
-                            cols[b][i] = nv;
-                            if (PIVOT && i == j) rowj[tix[b]] = nv;
-                        }
+                        if (b < nb) cols[b][i] = fma(-f[b], xi, cols[b][i]);
                 }
             } else if (PIVOT && threadIdx.x == 0) {
                 for (int b = 0; b < nb; ++b) rowj[tix[b]] = cols[b][j];
@@ -279,7 +283,7 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
     if (!PIVOT && !g.sync()) return false;
     if (prev_p >= 0 && prev_p % g.size == g.rank) {
         double* cq = A + cm(0, prev_p, lda);
-        for (int i = n + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i];
+        for (int i = n + threadIdx.x; i < m; i += blockDim.x) cq[i] = vs[i] * prev_rden;
         if (threadIdx.x == 0) cq[n - 1] = prev_beta;
     }
     __syncthreads();
@@ -292,10 +296,10 @@ __device__ bool hh_qr(const Group& g, int m, int n, double* A, int lda, double* 
 // CTAs can split them without synchronizing. If c_ident >= 0 the block [c0, c1) of C holds
 // columns c_ident.. of the identity, which H_j leaves untouched for j > column index:
 // those reflectors are skipped (valid for trans = false only, where H_{k-1} acts first).
-__device__ void apply_q_cols(bool trans, int mrows, int k, const double* Vr, int ldv,
+__device__ inline void apply_q_cols(bool trans, int mrows, int k, const double* Vr, int ldv,
                              const double* tau, double* C, int ldc, int c0, int c1, int c_ident)
 {
-    __shared__ double red[kApplyBatch * 32];
+    __shared__ double red[kApplyBatch * 33];
     for (int cb = c0; cb < c1; cb += kApplyBatch) {
         int nb = min(kApplyBatch, c1 - cb);
         double* cols[kApplyBatch];
@@ -318,21 +322,10 @@ __device__ void apply_q_cols(bool trans, int mrows, int k, const double* Vr, int
                 for (int b = 0; b < kApplyBatch; ++b)
                     if (b < nb) acc[b] = fma(vi, cols[b][i], acc[b]);
             }
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-            for (int b = 0; b < kApplyBatch; ++b) acc[b] = warp_sum(acc[b]);
-            __syncthreads();
-            if (lane == 0) {
-#pragma unroll
-                for (int b = 0; b < kApplyBatch; ++b) red[b * 32 + wid] = acc[b];
-            }
-            __syncthreads();
             double w[kApplyBatch];
+            block_sum_multi<kApplyBatch>(acc, red, w);
 #pragma unroll
-            for (int b = 0; b < kApplyBatch; ++b) {
-                double r = (lane < nw) ? red[b * 32 + lane] : 0.0;
-                w[b] = warp_sum(r) * tj;
-            }
+            for (int b = 0; b < kApplyBatch; ++b) w[b] *= tj;
             for (int i = j + threadIdx.x; i < mrows; i += blockDim.x) {
                 double vi = (i == j) ? 1.0 : v[i];
 #pragma unroll

@@ -1,13 +1,501 @@
-// svd_batched.cu -- placeholder until the persistent batched kernel lands.
+// svd_batched.cu -- Algorithm 4 for thousands of independent matrices of uneven sizes in one
+// persistent launch.
+//
+// Each CTA repeatedly takes the next matrix from a work queue ordered largest first (by
+// n^2 m, sorted on the host) and runs the whole pipeline of Algorithm 4 on it alone: the
+// stage routines are the same device functions the single-matrix path spreads over all SMs,
+// called with a one-CTA group whose barrier is __syncthreads. Every CTA owns a workspace
+// slot (its QRCP matrix, X, U_low, B, Y, V_acc, vectors and a state block) reused for each
+// matrix it takes. Per-matrix convergence: every matrix runs its own sweep loops; its status
+// bits go to info[i].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm.cuh"
 #include "internal.h"
+#include "qr.cuh"
+#include "sweep.cuh"
 
 namespace mpj {
 
-int svd_batched(mpjsvd_ctx*, int, const int*, const int*, const int*, const double* const*,
-                double* const*, double* const*, double* const*, double, int*)
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWLow = 8;
+constexpr int kBatchWWork = 8;
+
+struct BatchArgs {
+    int batch;
+    const int* order;        // matrix indices, largest first
+    const int* m;
+    const int* n;
+    const int* lda;
+    const double* const* A;
+    double* const* U;
+    double* const* S;
+    double* const* V;
+    int* info;
+    unsigned int* queue;     // work counter (zeroed before the launch)
+    char* slots;             // per-CTA workspace
+    size_t slot_bytes;
+    int max_m, max_n;
+    mpjsvd_params P;
+    double tol;
+};
+
+// Offsets inside a slot for (max_m, max_n).
+struct SlotLayout {
+    size_t st, wq, wql, tau, perm, x, xl, g, cn, sigl, ord, ul, bq, tau2, perm2, y, vacc, sig,
+        ord2, total;
+};
+
+__host__ __device__ inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+__host__ __device__ inline SlotLayout slot_layout(int M, int N)
 {
-    set_last_error("mpjsvd_svd_batched", cudaErrorNotSupported);
-    return MPJSVD_ERR_CUDA;
+    SlotLayout L;
+    size_t o = 0;
+    size_t nn = (size_t)N * N, mn = (size_t)M * N;
+    auto put = [&](size_t bytes) {
+        size_t at = o;
+        o += al256(bytes ? bytes : 16);
+        return at;
+    };
+    L.st = put(sizeof(DevState));
+    L.wq = put(8 * mn);
+    L.wql = put(8 * mn);
+    L.tau = put(8 * (size_t)N);
+    L.perm = put(4 * (size_t)N);
+    L.x = put(8 * nn);
+    L.xl = put(4 * nn);
+    L.g = put(4 * nn);
+    L.cn = put(8 * (size_t)N);
+    L.sigl = put(4 * (size_t)N);
+    L.ord = put(4 * (size_t)N);
+    L.ul = put(8 * nn);
+    L.bq = put(8 * nn);
+    L.tau2 = put(8 * (size_t)N);
+    L.perm2 = put(4 * (size_t)N);
+    L.y = put(8 * nn);
+    L.vacc = put(8 * nn);
+    L.sig = put(8 * (size_t)N);
+    L.ord2 = put(4 * (size_t)N);
+    L.total = o;
+    return L;
+}
+
+// ---- CTA-level building blocks (the single-matrix path has grid-wide versions)
+
+template <typename T>
+__device__ void cta_colnorms(int rows, int cols, const T* X, int ld, T* out)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < cols; c += nw) {
+        const T* col = X + cm(0, c, ld);
+        T s = T(0);
+        for (int i = lane; i < rows; i += 32) s = fma(col[i], col[i], s);
+        s = warp_sum(s);
+        if (lane == 0) out[c] = sqrt(s);
+    }
+    __syncthreads();
+}
+
+// order[rank] = index, descending stable; NaN keys rank last.
+template <typename T>
+__device__ void cta_rank_desc(int n, const T* key, int* order)
+{
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        T kj = key[j];
+        kj = (kj == kj) ? kj : T(-1);
+        int r = 0;
+        for (int i = 0; i < n; ++i) {
+            T ki = key[i];
+            ki = (ki == ki) ? ki : T(-1);
+            r += (ki > kj) || (ki == kj && i < j);
+        }
+        order[r] = j;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void cta_gemm(const GemmArgs& g)
+{
+    int tiles_m = (g.M + kGemmBM - 1) / kGemmBM;
+    int tiles_n = (g.N + kGemmBN - 1) / kGemmBN;
+    for (int t = 0; t < tiles_m * tiles_n; ++t)
+        gemm_tile<T>(g, (t % tiles_m) * kGemmBM, (t / tiles_m) * kGemmBN);
+    __syncthreads();
+}
+
+// Final assembly of one matrix (as k_finalize of the single-matrix path).
+__device__ void cta_finalize(int m, int n, const double* Y, const double* Vacc, const double* sig,
+                             const int* order, const int* jpvt, int precond, double* U, double* S,
+                             double* V, int* status)
+{
+    __shared__ double s_val[32];
+    __shared__ int s_row[32];
+    __shared__ double s_sign;
+    const bool rt = (precond != MPJSVD_PRECOND_R);
+    for (int k = 0; k < n; ++k) {
+        int j = order[k];
+        double sj = sig[j];
+        const double* y = Y + cm(0, j, n);
+        const double* va = Vacc + cm(0, j, n);
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double vr = rt ? ((sj > 0.0) ? y[i] / sj : 0.0) : va[i];
+            double a = fabs(vr);
+            int row = jpvt[i];
+            if (a > bv || (a == bv && row < br)) { bv = a; br = row; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            int orow = __shfl_xor_sync(0xffffffffu, br, o);
+            if (ov > bv || (ov == bv && orow < br)) { bv = ov; br = orow; }
+        }
+        if ((threadIdx.x & 31) == 0) { s_val[threadIdx.x >> 5] = bv; s_row[threadIdx.x >> 5] = br; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b2 = -1.0;
+            int r2 = 0x7fffffff;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (s_val[w] > b2 || (s_val[w] == b2 && s_row[w] < r2)) { b2 = s_val[w]; r2 = s_row[w]; }
+            s_sign = 1.0;
+            s_row[0] = r2;
+        }
+        __syncthreads();
+        int rbest = s_row[0];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            if (jpvt[i] == rbest) {
+                double vr = rt ? ((sj > 0.0) ? y[i] / sj : 0.0) : va[i];
+                s_sign = (vr < 0.0) ? -1.0 : 1.0;
+            }
+        }
+        __syncthreads();
+        double sg = s_sign;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double ux = (sj > 0.0) ? y[i] / sj : 0.0;
+            double uR = rt ? va[i] : ux;
+            double vR = rt ? ux : va[i];
+            U[cm(i, k, m)] = sg * uR;
+            V[cm(jpvt[i], k, n)] = sg * vR;
+        }
+        for (int i = n + threadIdx.x; i < m; i += blockDim.x) U[cm(i, k, m)] = 0.0;
+        if (threadIdx.x == 0) {
+            S[k] = sj;
+            if (sj == 0.0) *status |= MPJSVD_STATUS_ZERO_SIGMA;
+        }
+        __syncthreads();
+    }
+}
+
+// The whole of Algorithm 4 for one matrix by one CTA. Returns the status bits.
+__device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* smem)
+{
+    const int m = B.m[mat], n = B.n[mat], lda = B.lda[mat];
+    const double* A = B.A[mat];
+    double* U = B.U[mat];
+    double* S = B.S[mat];
+    double* V = B.V[mat];
+    const mpjsvd_params& P = B.P;
+    SlotLayout L = slot_layout(B.max_m, B.max_n);
+    DevState* st = (DevState*)(slot + L.st);
+    double* Wq = (double*)(slot + L.wq);
+    double* WqL = (double*)(slot + L.wql);
+    double* tau = (double*)(slot + L.tau);
+    int* perm = (int*)(slot + L.perm);
+    double* X = (double*)(slot + L.x);
+    float* Xl = (float*)(slot + L.xl);
+    float* G = (float*)(slot + L.g);
+    double* cn = (double*)(slot + L.cn);
+    float* sigl = (float*)(slot + L.sigl);
+    int* ord = (int*)(slot + L.ord);
+    double* Ul = (double*)(slot + L.ul);
+    double* Bq = (double*)(slot + L.bq);
+    double* tau2 = (double*)(slot + L.tau2);
+    int* perm2 = (int*)(slot + L.perm2);
+    double* Y = (double*)(slot + L.y);
+    double* Vacc = (double*)(slot + L.vacc);
+    double* sig = (double*)(slot + L.sig);
+    int* ord2 = (int*)(slot + L.ord2);
+    const size_t nn = (size_t)n * n;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    __shared__ int s_flag;
+    __shared__ int s_status;
+
+    // state block: barrier words unused (group of one CTA), counters zeroed
+    for (size_t i = tid; i < sizeof(DevState) / 4; i += nthr) ((int*)st)[i] = 0;
+    if (tid == 0) { s_flag = 0; s_status = 0; }
+    __syncthreads();
+
+    // ---- copy A, check finiteness
+    int bad = 0;
+    for (size_t e = tid; e < (size_t)m * n; e += nthr) {
+        int i = (int)(e % m), j = (int)(e / m);
+        double v = A[cm(i, j, lda)];
+        if (!isfinite(v)) bad = 1;
+        Wq[cm(i, j, m)] = v;
+    }
+    if (__syncthreads_or(bad)) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        for (size_t e = tid; e < (size_t)m * n; e += nthr) U[e] = qnan;
+        for (size_t e = tid; e < nn; e += nthr) V[e] = qnan;
+        for (int e = tid; e < n; e += nthr) S[e] = qnan;
+        return MPJSVD_STATUS_NONFINITE;
+    }
+
+    // ---- [3.1] QRCP of A (one CTA)
+    Group g1{0, 1, st};
+    hh_qr<true>(g1, m, n, Wq, m, tau, perm, (double*)smem);
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const double* src = Wq + cm(0, perm[j], m);
+        double* dst = WqL + cm(0, j, m);
+        for (int i = tid; i < m; i += nthr) dst[i] = src[i];
+    }
+    for (size_t e = tid; e < nn; e += nthr) {
+        int i = (int)(e % n), j = (int)(e / n);
+        double v;
+        if (P.precond == MPJSVD_PRECOND_R) v = (i <= j) ? WqL[cm(i, j, m)] : 0.0;
+        else v = (i >= j) ? WqL[cm(j, i, m)] : 0.0;
+        X[e] = v;
+    }
+    __syncthreads();
+
+    // ---- [3.5] special cases
+    int gate = 0;
+    {
+        cta_colnorms<double>(n, n, X, n, cn);
+        if (tid == 0) {
+            double mx = 0.0;
+            for (int j = 0; j < n; ++j) mx = fmax(mx, cn[j]);
+            double r00 = fabs(WqL[0]), rnn = fabs(WqL[cm(n - 1, n - 1, m)]);
+            double cond = (rnn > 0.0) ? r00 / rnn : INFINITY;
+            int ntrail = (int)ceil(P.trailing_frac * (double)n);
+            int small = ntrail > 0;
+            for (int j = n - ntrail; j < n; ++j)
+                if (cn[j] > 2.44140625e-04 * mx) { small = 0; break; }
+            int branch;
+            if (P.mode == MPJSVD_MODE_PLAIN) branch = 4;
+            else if (P.mode == MPJSVD_MODE_MIXED) branch = 0;
+            else if (cond <= P.tol_cond_coef * pow((double)n, 0.25)) branch = 1;
+            else if (small) branch = 2;
+            else branch = -1;
+            s_flag = branch;
+        }
+        __syncthreads();
+        if (s_flag == -1) {  // orth test: Xt = low(X) D^-1, max |Xt^T Xt - I|
+            const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+            for (int c = wid; c < n; c += nw) {
+                const double* col = X + cm(0, c, n);
+                float s = 0.0f;
+                for (int i = lane; i < n; i += 32) { float v = (float)col[i]; s = fmaf(v, v, s); }
+                s = warp_sum(s);
+                float d = sqrtf(s);
+                for (int i = lane; i < n; i += 32) {
+                    float v = (float)col[i];
+                    Xl[cm(i, c, n)] = (d > 0.0f) ? v / d : 0.0f;
+                }
+            }
+            __syncthreads();
+            GemmArgs ga;
+            ga.M = n; ga.N = n; ga.K = n; ga.A = Xl; ga.lda = n; ga.transA = true;
+            ga.B = Xl; ga.ldb = n; ga.transB = false; ga.C = G; ga.ldc = n;
+            ga.klo_from_row = (P.precond != MPJSVD_PRECOND_R);
+            ga.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
+            cta_gemm<float>(ga);
+            float mx = 0.0f;
+            for (size_t e = tid; e < nn; e += nthr) {
+                int i = (int)(e % n), j = (int)(e / n);
+                mx = fmaxf(mx, fabsf(G[e] - (i == j ? 1.0f : 0.0f)));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            __shared__ float s_mx[32];
+            if (lane == 0) s_mx[wid] = mx;
+            __syncthreads();
+            if (tid == 0) {
+                float m2 = 0.0f;
+                for (int w = 0; w < nw; ++w) m2 = fmaxf(m2, s_mx[w]);
+                s_flag = (m2 <= P.tol_orth) ? 3 : 0;
+            }
+            __syncthreads();
+        }
+        gate = (s_flag == 0);
+    }
+
+    // ---- [3.2]-[3.3] low-precision stage and switch, or Y = X, V_acc = I
+    if (gate) {
+        for (size_t e = tid; e < nn; e += nthr) Xl[e] = (float)X[e];
+        __syncthreads();
+        SweepDims D;
+        D.n = n; D.mX = n; D.ldX = n; D.nV = 0; D.ldV = n; D.w = kBatchWLow;
+        int nb = (n + kBatchWLow - 1) / kBatchWLow;
+        D.k = max(2, nb + (nb & 1));
+        D.maxsweep = min(P.maxsweep, 64);
+        D.tol = sqrt((double)n) * 5.9604644775390625e-08;
+        VisitSmem<float, kBatchWLow> sml = carve_visit_smem<float, kBatchWLow>(smem, n, false);
+        bool conv = false;
+        jacobi_sweeps<float, false, kBatchWLow>(g1, D, Xl, nullptr, st->rot_sweep[0], sml, &conv);
+        if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
+        __syncthreads();
+        cta_colnorms<float>(n, n, Xl, n, sigl);
+        cta_rank_desc<float>(n, sigl, ord);
+        for (size_t e = tid; e < nn; e += nthr) {
+            int i = (int)(e % n), r = (int)(e / n);
+            int j = ord[r];
+            float s = sigl[j];
+            Ul[e] = (s > 0.0f) ? (double)(Xl[cm(i, j, n)] / s) : 0.0;
+        }
+        __syncthreads();
+        GemmArgs gb;
+        gb.M = n; gb.N = n; gb.K = n; gb.A = X; gb.lda = n; gb.transA = true;
+        gb.B = Ul; gb.ldb = n; gb.transB = false; gb.C = Bq; gb.ldc = n;
+        gb.klo_from_row = (P.precond != MPJSVD_PRECOND_R);
+        gb.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
+        cta_gemm<double>(gb);
+        hh_qr<false>(g1, n, n, Bq, n, tau2, perm2, (double*)smem);
+        for (size_t e = tid; e < nn; e += nthr) Vacc[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+        __syncthreads();
+        apply_q_cols(false, n, n, Bq, n, tau2, Vacc, n, 0, n, 0);
+        __syncthreads();
+        GemmArgs gy;
+        gy.M = n; gy.N = n; gy.K = n; gy.A = X; gy.lda = n; gy.transA = false;
+        gy.B = Vacc; gy.ldb = n; gy.transB = false; gy.C = Y; gy.ldc = n;
+        gy.klo_from_row = (P.precond == MPJSVD_PRECOND_R);
+        gy.khi_from_row = (P.precond != MPJSVD_PRECOND_R);
+        cta_gemm<double>(gy);
+    } else {
+        for (size_t e = tid; e < nn; e += nthr) {
+            Y[e] = X[e];
+            Vacc[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+    }
+
+    // ---- [3.4] binary64 refinement with V
+    {
+        SweepDims D;
+        D.n = n; D.mX = n; D.ldX = n; D.nV = n; D.ldV = n; D.w = kBatchWWork;
+        int nb = (n + kBatchWWork - 1) / kBatchWWork;
+        D.k = max(2, nb + (nb & 1));
+        D.maxsweep = min(P.maxsweep, 64);
+        D.tol = (B.tol > 0.0) ? B.tol : sqrt((double)n) * 1.1102230246251565e-16;
+        VisitSmem<double, kBatchWWork> smw = carve_visit_smem<double, kBatchWWork>(smem, n, true);
+        bool conv = false;
+        jacobi_sweeps<double, true, kBatchWWork>(g1, D, Y, Vacc, st->rot_sweep[1], smw, &conv);
+        if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
+        __syncthreads();
+    }
+
+    // ---- assembly
+    cta_colnorms<double>(n, n, Y, n, sig);
+    cta_rank_desc<double>(n, sig, ord2);
+    cta_finalize(m, n, Y, Vacc, sig, ord2, perm, P.precond, U, S, V, &s_status);
+    __syncthreads();
+    apply_q_cols(false, m, n, WqL, m, tau, U, m, 0, n, -1);
+    __syncthreads();
+    return s_status;
+}
+
+__global__ void k_batched(BatchArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_idx;
+    char* slot = B.slots + (size_t)blockIdx.x * B.slot_bytes;
+    while (true) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        int idx = s_idx;
+        __syncthreads();
+        if (idx >= B.batch) break;
+        int mat = B.order[idx];
+        int status = svd_one(B, mat, slot, smem_raw);
+        if (threadIdx.x == 0) B.info[mat] = status;
+        __syncthreads();
+    }
+}
+
+static size_t batched_smem(int max_m, int max_n)
+{
+    size_t qr = hh_qr_smem_bytes(max_m, max_n, 1);
+    size_t s32 = sweep_smem_bytes<float, kBatchWLow>(max_n, false);
+    size_t s64 = sweep_smem_bytes<double, kBatchWWork>(max_n, true);
+    return std::max(qr, std::max(s32, s64));
+}
+
+int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,
+                const double* const* A, double* const* U, double* const* S, double* const* V,
+                double tol, int* info)
+{
+    int max_m = 1, max_n = 1;
+    for (int i = 0; i < batch; ++i) {
+        max_m = std::max(max_m, m[i]);
+        max_n = std::max(max_n, n[i]);
+    }
+    // largest first
+    std::vector<int> order(batch);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)n[a] * n[a] * m[a] > (double)n[b] * n[b] * m[b];
+    });
+    size_t smem = batched_smem(max_m, max_n);
+    cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("batched smem attribute", e);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, kBatchThreads, smem);
+    if (e != cudaSuccess) return cuda_fail("batched occupancy", e);
+    if (occ < 1) return cuda_fail("batched occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
+    int grid = std::min(batch, occ * h->num_sms);
+    SlotLayout L = slot_layout(max_m, max_n);
+    size_t slot_bytes = al256(L.total);
+    size_t meta = al256(sizeof(int) * (size_t)batch * 4) + 256;
+    int rc = ensure_buffer(&h->bws, &h->bws_bytes, meta + slot_bytes * (size_t)grid);
+    if (rc) return rc;
+    char* base = (char*)h->bws;
+    int* d_meta = (int*)base;  // order | m | n | lda
+    unsigned int* queue = (unsigned int*)(base + al256(sizeof(int) * (size_t)batch * 4));
+    std::vector<int> host(4 * (size_t)batch);
+    for (int i = 0; i < batch; ++i) {
+        host[i] = order[i];
+        host[batch + i] = m[i];
+        host[2 * batch + i] = n[i];
+        host[3 * batch + i] = lda[i];
+    }
+    // from pageable memory: the copy is staged before cudaMemcpyAsync returns, so the host
+    // vector may go out of scope afterwards
+    e = cudaMemcpyAsync(d_meta, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail("batched metadata copy", e);
+    e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), h->stream);
+    if (e != cudaSuccess) return cuda_fail("batched queue reset", e);
+    BatchArgs B;
+    B.batch = batch;
+    B.order = d_meta;
+    B.m = d_meta + batch;
+    B.n = d_meta + 2 * batch;
+    B.lda = d_meta + 3 * batch;
+    B.A = A;
+    B.U = U;
+    B.S = S;
+    B.V = V;
+    B.info = info;
+    B.queue = queue;
+    B.slots = base + meta;
+    B.slot_bytes = slot_bytes;
+    B.max_m = max_m;
+    B.max_n = max_n;
+    B.P = h->params;
+    B.tol = tol;
+    k_batched<<<grid, kBatchThreads, smem, h->stream>>>(B);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("batched launch", e);
+    h->launch_count = 1;
+    return 0;
 }
 
 }  // namespace mpj

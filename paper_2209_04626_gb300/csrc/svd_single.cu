@@ -25,7 +25,7 @@ namespace mpj {
 
 constexpr int kWmaxLow = 16;   // template bound on the FP32 block width
 constexpr int kWmaxWork = 8;   // template bound on the FP64 block width
-constexpr int kThreadsLow = 512;
+constexpr int kThreadsLow = 256;
 constexpr int kThreadsWork = 256;
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
@@ -319,16 +319,16 @@ __global__ void k_hhqr_plain(int m, int n, double* W, int ldw, double* tau, int*
     hh_qr<false>(g, m, n, W, ldw, tau, perm, qr_dyn);
 }
 
-template <typename T, bool WITH_V, int WMAX>
+template <typename T, bool WITH_V, int W>
 __global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, int gate_want)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (input_nonfinite(st)) return;
     if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
-    VisitSmem<T, WMAX> sm = carve_visit_smem<T, WMAX>(smem_raw, D.mX, D.w, WITH_V);
+    VisitSmem<T, W> sm = carve_visit_smem<T, W>(smem_raw, D.mX, WITH_V);
     Group g{(int)blockIdx.x, (int)gridDim.x, st};
     bool conv = false;
-    int sweeps = jacobi_sweeps<T, WITH_V, WMAX>(g, D, X, V, st->rot_sweep[phase], sm, &conv);
+    int sweeps = jacobi_sweeps<T, WITH_V, W>(g, D, X, V, st->rot_sweep[phase], sm, &conv);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps >= 0) {
         unsigned long long tot = 0;
         for (int s = 0; s < sweeps; ++s) tot += __ldcg(&st->rot_sweep[phase][s]);
@@ -485,20 +485,21 @@ static int pick_w(int n, int mX, bool low, int sms, int forced)
     if (forced > 0) {
         w = forced;
     } else if (low) {
-        w = 16;
+        w = 8;
     } else {
         w = even_ceil((n + 2 * sms - 1) / (2 * sms));
         if (n <= 512) w = std::max(w, 8);
     }
     w = std::min(w, std::min(wmax, smem_cap));
     w = std::min(w, std::max(1, n / 2));
-    if (w > 1 && (w & 1)) w -= 1;
-    return std::max(w, 1);
+    int p2 = 1;  // the kernels exist for power-of-two widths
+    while (p2 * 2 <= w) p2 *= 2;
+    return std::max(p2, 1);
 }
 
-template <typename T, bool WITH_V, int WMAX>
-static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
-                         double tol, DevState* st, int phase, int gate_want, int threads)
+template <typename T, bool WITH_V, int W>
+static int launch_sweeps_w(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
+                           double tol, DevState* st, int phase, int gate_want, int threads)
 {
     SweepDims D;
     D.n = n;
@@ -512,10 +513,15 @@ static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, i
     if (D.k < 2) D.k = 2;
     D.maxsweep = std::min(maxsweep, 64);
     D.tol = tol;
-    size_t smem = sweep_smem_bytes<T, WMAX>(mX, w, WITH_V);
-    auto kern = k_sweeps<T, WITH_V, WMAX>;
+    size_t smem = sweep_smem_bytes<T, W>(mX, WITH_V);
+    auto kern = k_sweeps<T, WITH_V, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail("sweep smem attribute", e);
+    // as many threads as the register file allows (512 when the kernel needs <= 128 each)
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return cuda_fail("sweep attributes", e);
+    threads = (fa.numRegs <= 128 && fa.maxThreadsPerBlock >= 512) ? 512 : 256;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return cuda_fail("sweep occupancy", e);
@@ -527,6 +533,25 @@ static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, i
     if (e != cudaSuccess) return cuda_fail("sweep launch", e);
     ++h->launch_count;
     return 0;
+}
+
+// Dispatch on the block width: FP64 kernels for w in {1, 2, 4, 8}, FP32 for {1, 2, 4, 8, 16}.
+template <typename T, bool WITH_V>
+static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
+                         double tol, DevState* st, int phase, int gate_want, int threads)
+{
+#define MPJ_SW(WW) \
+    return launch_sweeps_w<T, WITH_V, WW>(h, n, mX, X, V, w, maxsweep, tol, st, phase, gate_want, threads)
+    switch (w) {
+        case 1: MPJ_SW(1);
+        case 2: MPJ_SW(2);
+        case 4: MPJ_SW(4);
+        case 8: MPJ_SW(8);
+        default:
+            if constexpr (sizeof(T) == 4) { MPJ_SW(16); }
+            return cuda_fail("sweep block width", cudaErrorInvalidValue);
+    }
+#undef MPJ_SW
 }
 
 static int launch_hhqr(mpjsvd_ctx* h, bool pivot, int m, int n, double* W, int ldw, double* tau,
@@ -673,7 +698,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     if (P.mode != MPJSVD_MODE_PLAIN) {
         k_to_float<<<egrid, T256, 0, s>>>(nn, X, Xl, st); ++h->launch_count;
         const double tol_low = std::sqrt((double)n) * 5.9604644775390625e-08;
-        if ((rc = launch_sweeps<float, false, kWmaxLow>(h, n, n, Xl, nullptr, w_low, P.maxsweep,
+        if ((rc = launch_sweeps<float, false>(h, n, n, Xl, nullptr, w_low, P.maxsweep,
                                                         tol_low, st, 0, 1, kThreadsLow)))
             return rc;
         k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
@@ -710,7 +735,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
 
     // ---- [3.4] binary64 refinement with V accumulation
     const double tol_work = (tol > 0.0) ? tol : std::sqrt((double)n) * 1.1102230246251565e-16;
-    if ((rc = launch_sweeps<double, true, kWmaxWork>(h, n, n, Y, Vacc, w_work, P.maxsweep, tol_work,
+    if ((rc = launch_sweeps<double, true>(h, n, n, Y, Vacc, w_work, P.maxsweep, tol_work,
                                                      st, 1, -1, kThreadsWork)))
         return rc;
     record(h, 5);

@@ -148,6 +148,7 @@ def mpjsvd_last_error():
     return load_library().mpjsvd_last_error().decode()
 
 
+
 # ---------------------------------------------------------------- conveniences
 
 def colmajor(x, device=None):
@@ -201,6 +202,30 @@ class Handle:
                         V.data_ptr(), tol)
         _check(rc, "mpjsvd_svd")
         return U, S, V
+
+    def svd_batched(self, mats, tol=0.0):
+        """Thin SVDs of a list of CUDA float64 (m_i, n_i) tensors in one persistent launch.
+        Returns (list of U, list of S, list of V, info tensor)."""
+        import numpy as np
+        dev = mats[0].device
+        mats = [A if _is_colmajor(A) else colmajor(A, dev) for A in mats]
+        b = len(mats)
+        m = np.array([A.shape[0] for A in mats], dtype=np.int32)
+        n = np.array([A.shape[1] for A in mats], dtype=np.int32)
+        lda = np.array([A.stride(1) for A in mats], dtype=np.int32)
+        Us = [empty_colmajor(int(mi), int(ni), dev) for mi, ni in zip(m, n)]
+        Ss = [torch.empty(int(ni), dtype=torch.float64, device=dev) for ni in n]
+        Vs = [empty_colmajor(int(ni), int(ni), dev) for ni in n]
+        ptr = lambda ts: torch.tensor([t.data_ptr() for t in ts], dtype=torch.int64, device=dev)
+        pA, pU, pS, pV = ptr(mats), ptr(Us), ptr(Ss), ptr(Vs)
+        info = torch.zeros(b, dtype=torch.int32, device=dev)
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(dev).cuda_stream)
+        rc = mpjsvd_svd_batched(self.h, b, m.ctypes.data, n.ctypes.data, lda.ctypes.data,
+                                pA.data_ptr(), pU.data_ptr(), pS.data_ptr(), pV.data_ptr(), tol,
+                                info.data_ptr())
+        _check(rc, "mpjsvd_svd_batched")
+        self._keep = (pA, pU, pS, pV)  # pointer arrays live until the next call
+        return Us, Ss, Vs, info
 
     def stats(self):
         return mpjsvd_get_stats(self.h)
