@@ -145,6 +145,25 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
                         const double* V, const double* gU, const double* gS, const double* gV,
                         double* gA, double gap_tol, int* n_flagged);
 
+/* Allocation-free thin SVD of one small matrix (the paper has no counterpart: this is a
+ * deployment variant of mpjsvd_svd). It takes no handle and calls no cudaMalloc, cudaFree or
+ * allocating library routine, for callers that cannot allocate device memory: code whose
+ * allocator owns the GPU's memory up front, latency-critical loops where an allocation's
+ * implicit device synchronization is not acceptable, or code that must not grow its memory
+ * footprint after start-up. Its scratch is one static device array of 6 MiB that every GPU
+ * loading this library holds until the process exits.
+ *   m, n : 1 <= n <= m, m <= 512, n <= 256 (larger sizes return -1 / -2 with a message in
+ *          mpjsvd_last_error())
+ *   A, U, S, V, lda, tol : as in mpjsvd_svd (device pointers, default parameters,
+ *          MPJSVD_MODE_AUTO)
+ *   cuda_stream : the stream the work is enqueued on (cudaStream_t; NULL = legacy stream)
+ * The first call on a device looks up the scratch array's device address (once per device,
+ * with that device current); make that first call before any stream capture. Every call
+ * shares the scratch array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be ordered by the caller. Numeric status is not reported (no handle). */
+int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+                       double tol, void* cuda_stream);
+
 /* Synchronize the handle's stream and copy the stats of the last mpjsvd_svd call. */
 int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st);
 

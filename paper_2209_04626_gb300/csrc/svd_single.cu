@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "gemm.cuh"
@@ -784,4 +785,97 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     return 0;
 }
 
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of mpjsvd_svd for callers that must not allocate device memory.
+// Its scratch (the per-call state block plus the same workspace layout mpjsvd_svd uses) is
+// one file-scope device array of kNoAllocBytes, present on every GPU that loads this
+// library until the process exits. Every call shares it, so calls that overlap on the GPU
+// (different streams, or different host threads without ordering) race on it. The state
+// block is cleared by each call itself (svd_single's first memset), and the workspace holds
+// nothing that must start at zero.
+// ------------------------------------------------------------------------------------
+
+constexpr size_t kNoAllocBytes = size_t(6) << 20;  // 6 MiB
+constexpr int kNoAllocMaxM = 512;
+constexpr int kNoAllocMaxN = 256;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device. In host code the symbol
+// g_noalloc_scratch is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+static int noalloc_scratch(int dev, void** out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return cuda_fail("mpjsvd_svd_noalloc: device index", cudaErrorInvalidDevice);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: cudaGetSymbolAddress", e);
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return 0;
+}
+
+static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S, double* V,
+                       double tol, cudaStream_t stream)
+{
+    if (m > kNoAllocMaxM || n > kNoAllocMaxN)
+        return cuda_fail("mpjsvd_svd_noalloc: m > 512 or n > 256 exceeds the static scratch",
+                         cudaErrorInvalidValue);
+    const size_t state_bytes = align256(sizeof(DevState));
+    SingleLayout L = single_layout(m, n, false);
+    if (state_bytes + L.total > kNoAllocBytes)
+        return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
+                         cudaErrorInvalidValue);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: cudaGetDevice", e);
+    void* base = nullptr;
+    int rc = noalloc_scratch(dev, &base);
+    if (rc) return rc;
+    mpjsvd_ctx ctx;
+    memset(&ctx, 0, sizeof(ctx));
+    ctx.device = dev;
+    e = cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: SM count", e);
+    ctx.stream = stream;
+    mpjsvd_default_params(&ctx.params);
+    ctx.dstate = base;
+    ctx.ws = (char*)base + state_bytes;
+    ctx.ws_bytes = kNoAllocBytes - state_bytes;  // ensure_buffer never allocates below this
+    ctx.have_events = false;
+    return svd_single(&ctx, m, n, A, lda, U, S, V, tol);
+}
+
 }  // namespace mpj
+
+extern "C" int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S,
+                                  double* V, double tol, void* cuda_stream)
+{
+    if (m < 1 || m < n) return -1;
+    if (n < 1) return -2;
+    if (m > mpj::kNoAllocMaxM) {
+        mpj::set_last_error("mpjsvd_svd_noalloc: m exceeds 512, the static scratch limit",
+                            cudaErrorInvalidValue);
+        return -1;
+    }
+    if (n > mpj::kNoAllocMaxN) {
+        mpj::set_last_error("mpjsvd_svd_noalloc: n exceeds 256, the static scratch limit",
+                            cudaErrorInvalidValue);
+        return -2;
+    }
+    if (!A) return -3;
+    if (lda < m) return -4;
+    if (!U) return -5;
+    if (!S) return -6;
+    if (!V) return -7;
+    if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -8;
+    return mpj::svd_noalloc(m, n, A, lda, U, S, V, tol, (cudaStream_t)cuda_stream);
+}

@@ -23,7 +23,7 @@ STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2
 
 EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsvd_set_params",
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
-           "mpjsvd_destroy", "mpjsvd_last_error"]
+           "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -75,6 +75,7 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
     L.mpjsvd_destroy.argtypes = [_vp]
     L.mpjsvd_last_error.restype = ctypes.c_char_p
+    L.mpjsvd_svd_noalloc.argtypes = [_i, _i, _vp, _i, _vp, _vp, _vp, _d, _vp]
     _lib = L
     return L
 
@@ -147,6 +148,12 @@ def mpjsvd_destroy(h):
 def mpjsvd_last_error():
     return load_library().mpjsvd_last_error().decode()
 
+
+def mpjsvd_svd_noalloc(m, n, A_ptr, lda, U_ptr, S_ptr, V_ptr, tol=0.0, stream=None):
+    """Allocation-free SVD for m <= 512, n <= 256 (static device scratch, no handle)."""
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    return load_library().mpjsvd_svd_noalloc(m, n, _vp(A_ptr), lda, _vp(U_ptr), _vp(S_ptr),
+                                             _vp(V_ptr), tol, _vp(s))
 
 
 # ---------------------------------------------------------------- conveniences

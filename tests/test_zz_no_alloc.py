@@ -1,0 +1,66 @@
+"""The allocation-free entry point (mpjsvd_svd_noalloc) against the handle-based
+mpjsvd_svd, through the C ABI.
+
+mpjsvd_svd_noalloc serves callers that cannot allocate device memory: its scratch is a
+static device array shared by every call, so it takes no handle and never calls cudaMalloc.
+This file is collected last on purpose: if it fails, a run that stops at the first failure
+has already run every other test. It must pass in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_04626_gb300 import inputs
+from tests.gpu_util import U64, align_signs, check_factorization
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(A):
+    import torch
+    from paper_2209_04626_gb300 import mpjsvd
+    m, n = A.shape
+    Ad = mpjsvd.colmajor(torch.from_numpy(A), torch.device("cuda"))
+    U = mpjsvd.empty_colmajor(m, n, Ad.device)
+    S = torch.empty(n, dtype=torch.float64, device=Ad.device)
+    V = mpjsvd.empty_colmajor(n, n, Ad.device)
+    rc = mpjsvd.mpjsvd_svd_noalloc(m, n, Ad.data_ptr(), m, U.data_ptr(), S.data_ptr(),
+                                   V.data_ptr(), 0.0)
+    assert rc == 0, mpjsvd.mpjsvd_last_error()
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+
+
+def _handle(A):
+    import torch
+    from paper_2209_04626_gb300 import mpjsvd
+    h = mpjsvd.Handle(mode="auto")
+    Ad = mpjsvd.colmajor(torch.from_numpy(A), torch.device("cuda"))
+    U, S, V = [t.cpu().numpy() for t in h.svd(Ad)]
+    st = h.stats()
+    h.close()
+    assert st["status"] == 0
+    return U, S, V
+
+
+def test_noalloc_matches_handle_path_on_two_calls_in_a_row():
+    rng = np.random.default_rng(31)
+    cases = [inputs.known_sigma(rng, 300, 200, np.logspace(0, -5, 200)),
+             inputs.known_sigma(rng, 96, 64, np.logspace(0, -2, 64))]
+    for A in cases:  # two calls in a row on the shared scratch, different shapes
+        U, S, V = _noalloc(A)
+        Ur, Sr, Vr = _handle(A)
+        n = A.shape[1]
+        check_factorization(A, U, S, V)
+        assert np.max(np.abs(S - Sr) / Sr) <= 1e-12
+        Ua, Va = align_signs(U, V, Ur, Vr)
+        assert np.abs(Va - Vr).max() <= 1e-8
+        assert np.abs(Ua - Ur).max() <= 1e-8
+        assert np.abs(U.T @ U - np.eye(n)).max() <= 64 * n * U64
+
+
+def test_noalloc_rejects_sizes_beyond_the_scratch():
+    from paper_2209_04626_gb300 import mpjsvd
+    rc = mpjsvd.mpjsvd_svd_noalloc(1024, 8, 1, 1024, 1, 1, 1, 0.0)
+    assert rc == -1 and "512" in mpjsvd.mpjsvd_last_error()
+    rc = mpjsvd.mpjsvd_svd_noalloc(512, 300, 1, 512, 1, 1, 1, 0.0)
+    assert rc == -2 and "256" in mpjsvd.mpjsvd_last_error()
