@@ -44,6 +44,14 @@ struct DevState {
     double argmax_val[512];
 };
 
+// True once the call cannot produce meaningful output: a non-finite input, or a cooperative
+// stage that gave up on a bounded wait. Later stages then return at once.
+__device__ __forceinline__ bool call_failed(const DevState* st)
+{
+    return (*(volatile const int*)&st->status &
+            (MPJSVD_STATUS_NONFINITE | MPJSVD_STATUS_TIMEOUT)) != 0;
+}
+
 // Bounded grid barrier for a cooperative launch (all CTAs co-resident). Returns false
 // if the wait timed out or another CTA reported an error; callers then exit.
 __device__ __forceinline__ bool grid_sync(DevState* st)

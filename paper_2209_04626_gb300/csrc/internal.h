@@ -41,6 +41,15 @@ int cuda_fail(const char* where, cudaError_t e);
 // grow a device buffer to at least `bytes`
 int ensure_buffer(void** buf, size_t* cur, size_t bytes);
 
+struct SweepDims;
+struct DevState;
+
+// sweep stages (sweep_f32.cu, sweep_f64.cu): one cooperative launch each
+int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st, int phase,
+                      int gate_want, int* threads_out);
+int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
+                      int phase, int gate_want, int* threads_out);
+
 // single-matrix pipeline (svd_single.cu)
 int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U, double* S,
                double* V, double tol);

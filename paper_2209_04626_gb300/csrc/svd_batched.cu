@@ -50,7 +50,7 @@ struct BatchArgs {
 // Offsets inside a slot for (max_m, max_n).
 struct SlotLayout {
     size_t st, wq, wql, tau, perm, x, xl, g, cn, sigl, ord, ul, bq, tau2, perm2, y, vacc, sig,
-        ord2, total;
+        ord2, dsc, alph, total;
 };
 
 __host__ __device__ inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -84,6 +84,8 @@ __host__ __device__ inline SlotLayout slot_layout(int M, int N)
     L.vacc = put(8 * nn);
     L.sig = put(8 * (size_t)N);
     L.ord2 = put(4 * (size_t)N);
+    L.dsc = put(8 * (size_t)N);
+    L.alph = put(8 * (size_t)N);
     L.total = o;
     return L;
 }
@@ -228,6 +230,8 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
     const int tid = threadIdx.x, nthr = blockDim.x;
     __shared__ int s_flag;
     __shared__ int s_status;
+    __shared__ VisitShared<float, kBatchWLow> sm_low;
+    __shared__ VisitShared<double, kBatchWWork> sm_work;
 
     // state block: barrier words unused (group of one CTA), counters zeroed
     for (size_t i = tid; i < sizeof(DevState) / 4; i += nthr) ((int*)st)[i] = 0;
@@ -259,6 +263,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         double* dst = WqL + cm(0, j, m);
         for (int i = tid; i < m; i += nthr) dst[i] = src[i];
     }
+    __syncthreads();  // X below reads entries other threads gathered
     for (size_t e = tid; e < nn; e += nthr) {
         int i = (int)(e % n), j = (int)(e / n);
         double v;
@@ -339,9 +344,17 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         D.k = max(2, nb + (nb & 1));
         D.maxsweep = min(P.maxsweep, 64);
         D.tol = sqrt((double)n) * 5.9604644775390625e-08;
-        VisitSmem<float, kBatchWLow> sml = carve_visit_smem<float, kBatchWLow>(smem, n, false);
+        float* dscf = (float*)(slot + L.dsc);
+        D.dsc = dscf;
+        D.alph = slot + L.alph;
+        for (int j = tid; j < n; j += nthr) dscf[j] = 1.0f;
+        __syncthreads();
         bool conv = false;
-        jacobi_sweeps<float, false, kBatchWLow>(g1, D, Xl, nullptr, st->rot_sweep[0], sml, &conv);
+        if (n <= nthr)
+            jacobi_sweeps<float, false, kBatchWLow, 1>(g1, D, Xl, nullptr, st->rot_sweep[0], sm_low, &conv);
+        else
+            jacobi_sweeps<float, false, kBatchWLow, 2>(g1, D, Xl, nullptr, st->rot_sweep[0], sm_low, &conv);
+        fold_scales_cols<float>(g1, n, n, Xl, n, 0, nullptr, n, dscf);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();
         cta_colnorms<float>(n, n, Xl, n, sigl);
@@ -386,9 +399,17 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         D.k = max(2, nb + (nb & 1));
         D.maxsweep = min(P.maxsweep, 64);
         D.tol = (B.tol > 0.0) ? B.tol : sqrt((double)n) * 1.1102230246251565e-16;
-        VisitSmem<double, kBatchWWork> smw = carve_visit_smem<double, kBatchWWork>(smem, n, true);
+        double* dscd = (double*)(slot + L.dsc);
+        D.dsc = dscd;
+        D.alph = slot + L.alph;
+        for (int j = tid; j < n; j += nthr) dscd[j] = 1.0;
+        __syncthreads();
         bool conv = false;
-        jacobi_sweeps<double, true, kBatchWWork>(g1, D, Y, Vacc, st->rot_sweep[1], smw, &conv);
+        if (n <= nthr)
+            jacobi_sweeps<double, true, kBatchWWork, 1>(g1, D, Y, Vacc, st->rot_sweep[1], sm_work, &conv);
+        else
+            jacobi_sweeps<double, true, kBatchWWork, 2>(g1, D, Y, Vacc, st->rot_sweep[1], sm_work, &conv);
+        fold_scales_cols<double>(g1, n, n, Y, n, n, Vacc, n, dscd);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();
     }
@@ -421,13 +442,7 @@ __global__ void k_batched(BatchArgs B)
     }
 }
 
-static size_t batched_smem(int max_m, int max_n)
-{
-    size_t qr = hh_qr_smem_bytes(max_m, max_n, 1);
-    size_t s32 = sweep_smem_bytes<float, kBatchWLow>(max_n, false);
-    size_t s64 = sweep_smem_bytes<double, kBatchWWork>(max_n, true);
-    return std::max(qr, std::max(s32, s64));
-}
+static size_t batched_smem(int max_m, int max_n) { return hh_qr_smem_bytes(max_m, max_n, 1); }
 
 int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,
                 const double* const* A, double* const* U, double* const* S, double* const* V,

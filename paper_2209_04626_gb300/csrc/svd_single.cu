@@ -24,10 +24,8 @@
 
 namespace mpj {
 
-constexpr int kWmaxLow = 16;   // template bound on the FP32 block width
-constexpr int kWmaxWork = 8;   // template bound on the FP64 block width
-constexpr int kThreadsLow = 256;
-constexpr int kThreadsWork = 256;
+constexpr int kWmaxLow = 16;   // widest binary32 block
+constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
 
@@ -320,25 +318,6 @@ __global__ void k_hhqr_plain(int m, int n, double* W, int ldw, double* tau, int*
     hh_qr<false>(g, m, n, W, ldw, tau, perm, qr_dyn);
 }
 
-template <typename T, bool WITH_V, int W>
-__global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, int gate_want)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (input_nonfinite(st)) return;
-    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
-    VisitSmem<T, W> sm = carve_visit_smem<T, W>(smem_raw, D.mX, WITH_V);
-    Group g{(int)blockIdx.x, (int)gridDim.x, st};
-    bool conv = false;
-    int sweeps = jacobi_sweeps<T, WITH_V, W>(g, D, X, V, st->rot_sweep[phase], sm, &conv);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps >= 0) {
-        unsigned long long tot = 0;
-        for (int s = 0; s < sweeps; ++s) tot += __ldcg(&st->rot_sweep[phase][s]);
-        if (phase == 0) { st->sweeps_low = sweeps; st->rot_low = tot; }
-        else { st->sweeps_work = sweeps; st->rot_work = tot; }
-        if (!conv) atomicOr(&st->status, MPJSVD_STATUS_NOT_CONVERGED);
-    }
-}
-
 // Final assembly (Alg. 1 end; Alg. 4 last line). One CTA per output column k:
 //   j = order[k]; S[k] = sig[j]; U_X(:, j) = Y(:, j) / sig[j];
 //   precond R^T: U_R = V_acc(:, j), V_R = U_X(:, j);  precond R: U_R = U_X(:, j), V_R = V_acc(:, j)
@@ -424,14 +403,16 @@ __global__ void k_finalize(int m, int n, const double* __restrict__ Y, const dou
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct SingleLayout {
-    size_t off[24];
+    size_t off[32];  // >= L_COUNT (static_assert below)
     size_t total;
 };
 
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
-    L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_COUNT
+    L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
+    L_ALPH, L_COUNT
 };
+static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
 
 static SingleLayout single_layout(int m, int n, bool qr_first)
 {
@@ -462,6 +443,8 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_ORD2] = sizeof(int) * n;
     sz[L_BITS] = 256;
     sz[L_PERM2] = sizeof(int) * n;
+    sz[L_DSC] = sizeof(double) * n;
+    sz[L_ALPH] = sizeof(double) * n;
     SingleLayout L;
     size_t o = 0;
     for (int i = 0; i < L_COUNT; ++i) {
@@ -472,16 +455,23 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     return L;
 }
 
+static int sweep_blocks(int n, int w)
+{
+    int nb = (n + w - 1) / w;
+    return std::max(2, nb + (nb & 1));
+}
+
 static int even_ceil(int x) { return x <= 1 ? 1 : ((x + 1) & ~1); }
 
 // Block width of the sweeps. FP64 (work): just enough blocks to give every SM a visit per
-// round (the stage is FP64-throughput bound), capped by shared memory. FP32 (low): wide
-// blocks (the stage is latency bound: fewer rounds, fewer barriers).
+// round (the stage is FP64-throughput bound). FP32 (low): wide blocks (the stage is latency
+// bound: fewer rounds, fewer barriers). A visit keeps 2w columns x (mX / threads) rows in
+// registers, which caps w for tall X (<= 1024 threads, <= 32 doubles / 64 floats each).
 static int pick_w(int n, int mX, bool low, int sms, int forced)
 {
     int wmax = low ? kWmaxLow : kWmaxWork;
-    int elem = low ? 4 : 8;
-    int smem_cap = (int)((150 * 1024) / ((size_t)2 * mX * elem));
+    int rpt_min = std::max(2, (mX + 1023) / 1024);
+    int smem_cap = std::max(1, (low ? 64 : 32) / rpt_min);
     int w;
     if (forced > 0) {
         w = forced;
@@ -496,63 +486,6 @@ static int pick_w(int n, int mX, bool low, int sms, int forced)
     int p2 = 1;  // the kernels exist for power-of-two widths
     while (p2 * 2 <= w) p2 *= 2;
     return std::max(p2, 1);
-}
-
-template <typename T, bool WITH_V, int W>
-static int launch_sweeps_w(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
-                           double tol, DevState* st, int phase, int gate_want, int threads)
-{
-    SweepDims D;
-    D.n = n;
-    D.mX = mX;
-    D.ldX = mX;
-    D.nV = WITH_V ? n : 0;
-    D.ldV = n;
-    D.w = w;
-    int nb = (n + w - 1) / w;
-    D.k = nb + (nb & 1);
-    if (D.k < 2) D.k = 2;
-    D.maxsweep = std::min(maxsweep, 64);
-    D.tol = tol;
-    size_t smem = sweep_smem_bytes<T, W>(mX, WITH_V);
-    auto kern = k_sweeps<T, WITH_V, W>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail("sweep smem attribute", e);
-    // as many threads as the register file allows (512 when the kernel needs <= 128 each)
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, kern);
-    if (e != cudaSuccess) return cuda_fail("sweep attributes", e);
-    threads = (fa.numRegs <= 128 && fa.maxThreadsPerBlock >= 512) ? 512 : 256;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-    if (e != cudaSuccess) return cuda_fail("sweep occupancy", e);
-    if (occ < 1) return cuda_fail("sweep occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
-    int grid = std::min(D.k / 2, occ * h->num_sms);
-    grid = std::min(grid, 1024);
-    void* args[] = {&D, &X, &V, &st, &phase, &gate_want};
-    e = cudaLaunchCooperativeKernel((void*)kern, grid, threads, args, smem, h->stream);
-    if (e != cudaSuccess) return cuda_fail("sweep launch", e);
-    ++h->launch_count;
-    return 0;
-}
-
-// Dispatch on the block width: FP64 kernels for w in {1, 2, 4, 8}, FP32 for {1, 2, 4, 8, 16}.
-template <typename T, bool WITH_V>
-static int launch_sweeps(mpjsvd_ctx* h, int n, int mX, T* X, double* V, int w, int maxsweep,
-                         double tol, DevState* st, int phase, int gate_want, int threads)
-{
-#define MPJ_SW(WW) \
-    return launch_sweeps_w<T, WITH_V, WW>(h, n, mX, X, V, w, maxsweep, tol, st, phase, gate_want, threads)
-    switch (w) {
-        case 1: MPJ_SW(1);
-        case 2: MPJ_SW(2);
-        case 4: MPJ_SW(4);
-        case 8: MPJ_SW(8);
-        default:
-            if constexpr (sizeof(T) == 4) { MPJ_SW(16); }
-            return cuda_fail("sweep block width", cudaErrorInvalidValue);
-    }
-#undef MPJ_SW
 }
 
 static int launch_hhqr(mpjsvd_ctx* h, bool pivot, int m, int n, double* W, int ldw, double* tau,
@@ -640,6 +573,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     int* ord2 = (int*)ptr(L_ORD2);
     unsigned int* bits = (unsigned int*)ptr(L_BITS);
     int* perm2 = (int*)ptr(L_PERM2);
+    void* dsc = ptr(L_DSC);
+    void* alph = ptr(L_ALPH);
     DevState* st = (DevState*)h->dstate;
     cudaStream_t s = h->stream;
     const int T256 = 256;
@@ -699,9 +634,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     if (P.mode != MPJSVD_MODE_PLAIN) {
         k_to_float<<<egrid, T256, 0, s>>>(nn, X, Xl, st); ++h->launch_count;
         const double tol_low = std::sqrt((double)n) * 5.9604644775390625e-08;
-        if ((rc = launch_sweeps<float, false>(h, n, n, Xl, nullptr, w_low, P.maxsweep,
-                                                        tol_low, st, 0, 1, kThreadsLow)))
-            return rc;
+        SweepDims Dl;
+        Dl.n = n; Dl.mX = n; Dl.ldX = n; Dl.nV = 0; Dl.ldV = n; Dl.w = w_low;
+        Dl.k = sweep_blocks(n, w_low); Dl.maxsweep = std::min(P.maxsweep, 64); Dl.tol = tol_low;
+        Dl.dsc = dsc; Dl.alph = alph;
+        if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
         k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
         k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
         k_make_ul<<<std::min(n, egrid), T256, 0, s>>>(n, Xl, sigl, ord, Ul, st); ++h->launch_count;
@@ -736,9 +673,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
 
     // ---- [3.4] binary64 refinement with V accumulation
     const double tol_work = (tol > 0.0) ? tol : std::sqrt((double)n) * 1.1102230246251565e-16;
-    if ((rc = launch_sweeps<double, true>(h, n, n, Y, Vacc, w_work, P.maxsweep, tol_work,
-                                                     st, 1, -1, kThreadsWork)))
-        return rc;
+    SweepDims Dw;
+    Dw.n = n; Dw.mX = n; Dw.ldX = n; Dw.nV = n; Dw.ldV = n; Dw.w = w_work;
+    Dw.k = sweep_blocks(n, w_work); Dw.maxsweep = std::min(P.maxsweep, 64); Dw.tol = tol_work;
+    Dw.dsc = dsc; Dw.alph = alph;
+    if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
     record(h, 5);
 
     // ---- Sigma, U_X, sort, U = Q [U_R; 0], V = P V_R

@@ -65,15 +65,21 @@ def test_autograd_against_central_differences():
     L.backward()
     g = Ad.grad.detach().cpu().numpy()
     h = 1e-6
+    L0 = abs(L.item())
     for k in range(6):
         E = rng.standard_normal((m, n))
         Et = mpjsvd.colmajor(torch.from_numpy(E), torch.device("cuda"))
         with torch.no_grad():
-            lp = loss(Ad.detach() + h * Et).item()
-            lm = loss(Ad.detach() - h * Et).item()
-        fd = (lp - lm) / (2 * h)
+            fd = [(loss(Ad.detach() + s * Et).item() - loss(Ad.detach() - s * Et).item()) / (2 * s)
+                  for s in (h, 2 * h)]
         an = float(np.sum(g * E))
-        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (k, fd, an)
+        # central differences err by c h^2: estimate it from the 2h value (Richardson), plus
+        # the rounding of the loss divided by h
+        trunc = abs(fd[1] - fd[0]) / 3.0
+        rounding = 1e3 * 2.0 ** -53 * max(1.0, L0) / h
+        assert abs(fd[0] - an) <= 3.0 * trunc + rounding + 1e-9 * abs(an), (k, fd, an)
+        richardson = (4.0 * fd[0] - fd[1]) / 3.0
+        assert abs(richardson - an) <= abs(fd[0] - an) + rounding, (k, richardson, an)
 
 
 def test_differentiation_workload_large_member():
