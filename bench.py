@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--plain-steps", type=int, default=3)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch-count", type=int, default=4096)
     return p.parse_args()
 
 
@@ -125,6 +127,16 @@ def oracle_sample(A, sweeps_low, sweeps_work):
             "t_sweep32": t32, "t_sweep64": t64}
 
 
+def oracle_full(A):
+    """One complete oracle SVD (Algorithm 4, low-precision stage forced) of the workload."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    _, _, _, st = oracle.svd(A, mode="mixed")
+    dt = time.perf_counter() - t0
+    return dt, st
+
+
 def cpu_baseline_obj(res, sweeps_low, sweeps_work, m, n):
     return {"value": 1.0 / res["est_svd_s"], "unit": "SVDs/s", "cores": 1, "kind": "oracle",
             "sample": ("single-threaded C oracle on the %dx%d input: QR + QRCP (%.1f s), one "
@@ -135,6 +147,24 @@ def cpu_baseline_obj(res, sweeps_low, sweeps_work, m, n):
 
 
 # ------------------------------------------------------------------------------ dist
+
+def max_over_ranks(value, device):
+    """Maximum of a per-rank float over all ranks (the slowest rank's time); identity when
+    torch.distributed is not initialized. Ends with a barrier."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(world, steps, max_ms):
+    """Whole-job SVDs/s of `world` replicas that each ran `steps` SVDs in at most max_ms."""
+    return world * steps / (max_ms / 1000.0)
+
 
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -151,7 +181,7 @@ def reference_arm(args):
     import oracle
     oracle.lib()
     A = inputs.precision_2048x1024(m=args.m, n=args.n)
-    sweeps_low, sweeps_work = 8, 4  # typical counts of the mixed path on this input
+    sweeps_low, sweeps_work = 8, 5  # the oracle's own sweep counts on this input (mixed)
     for _ in range(args.warmup):
         oracle_sample(A, sweeps_low, sweeps_work)
     ests, samples = [], []
@@ -247,13 +277,9 @@ def ours(args):
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+    total_ms = max_over_ranks(total_ms, dev)
     st = per_step_stats[-1]
-    value = world * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, args.steps, total_ms)
 
     # roofline of the dominant kernel: the FP64 refinement sweeps
     work_ms = [s["ms_work"] for s in per_step_stats]
@@ -313,11 +339,38 @@ def ours(args):
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = world * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
 
+    # the uneven batch: 4096 matrices, one persistent launch per step
+    batched = None
+    if not args.no_batched:
+        mats, _, bm, bn, bk = inputs.batch_matrices(count=args.batch_count)
+        dmats = [mpjsvd.colmajor(torch.from_numpy(X), dev) for X in mats]
+        hb = mpjsvd.Handle(mode="mixed")
+        hb.svd_batched(dmats)
+        torch.cuda.synchronize()
+        bms = []
+        for k in range(3):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, _, binfo = hb.svd_batched(dmats)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bms.append(e0.elapsed_time(e1))
+        batched = {"workload": "4096 matrices, n ~ U{16..256}, m = n + U{0..n}, kappa = 10^U(1,8), "
+                               "sigma log-spaced, seed 2; mode mixed; one persistent launch",
+                   "count": len(mats), "svds_per_s": len(mats) / (statistics.mean(bms) / 1000.0),
+                   "ms": statistics.mean(bms), "nonzero_info": int((binfo != 0).sum().item())}
+        hb.close()
+        del dmats
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            res = oracle_sample(A_np, st["sweeps_low"], st["sweeps_work"])
-            cpu = cpu_baseline_obj(res, st["sweeps_low"], st["sweeps_work"], m, n)
+            dt, ost = oracle_full(A_np)
+            cpu = {"value": 1.0 / dt, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
+                   "sample": ("one complete SVD of the %dx%d workload by the single-threaded C "
+                              "oracle (Algorithm 4, low-precision stage forced; %d + %d sweeps), "
+                              "%.1f s" % (m, n, ost["sweeps_low"], ost["sweeps_work"], dt))}
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
                    "sample": "failed: %s" % ex}
@@ -350,9 +403,10 @@ def ours(args):
             "sweeps": {"low": st["sweeps_low"], "work": st["sweeps_work"],
                        "rot_low": st["rot_low"], "rot_work": st["rot_work"]},
             "fp64_gflops_whole_svd": flops_svd_fp64(m, n, st["sweeps_work"]) / (total_ms / args.steps) / 1e6,
-            "compare": {"plain_svds_per_s": 1000.0 / statistics.mean(pms),
-                        "plain_ms": statistics.mean(pms), "plain_sweeps_work": stp["sweeps_work"],
-                        "mixed_over_plain": statistics.mean(pms) / (total_ms / args.steps),
+            "compare": {"plain_svds_per_s": 1000.0 / statistics.mean(pms) if pms else None,
+                        "plain_ms": statistics.mean(pms) if pms else None,
+                        "plain_sweeps_work": stp["sweeps_work"],
+                        "mixed_over_plain": statistics.mean(pms) / (total_ms / args.steps) if pms else None,
                         "auto_branch": sta["branch_name"],
                         "max_rel_sigma_mixed_vs_plain": sig_rel_mixed_vs_plain},
             "accuracy": {"backward_fro": bw, "orth_U_max": orthU, "orth_V_max": orthV,
@@ -361,6 +415,7 @@ def ours(args):
                     "d2h_bytes_per_step": (m * n + n + n * n) * 8},
             "gpu_launches": int(sum(s["launches"] for s in per_step_stats)),
             "cpu_baseline": cpu,
+            "batched": batched,
             "clocks": clk,
             "wall_s": wall,
         }

@@ -40,8 +40,7 @@ struct DevState {
     double orth;
     double maxnorm;        // max column norm of X (branch test)
     unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
-    int argmax_idx[512];                   // QRCP: per-CTA candidate pivot
-    double argmax_val[512];
+    double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
 };
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative

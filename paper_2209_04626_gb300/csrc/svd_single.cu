@@ -308,6 +308,25 @@ __global__ void k_hhqr_piv(int m, int n, double* W, int ldw, double* tau, int* p
     hh_qr<true>(g, m, n, W, ldw, tau, perm, qr_dyn);
 }
 
+__global__ void k_hhqr_res_piv(int m, int n, double* W, int ldw, double* tau, int* perm,
+                               DevState* st, double* bcast)
+{
+    extern __shared__ double qr_dyn[];
+    if (input_nonfinite(st)) return;
+    Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    hh_qr_res<true>(g, m, n, W, ldw, tau, perm, qr_dyn, bcast, nullptr);
+}
+
+__global__ void k_hhqr_res_plain(int m, int n, double* W, int ldw, double* tau, int* perm,
+                                 DevState* st, double* bcast, int* flags, int gate_want)
+{
+    extern __shared__ double qr_dyn[];
+    if (input_nonfinite(st)) return;
+    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
+    Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    hh_qr_res<false>(g, m, n, W, ldw, tau, perm, qr_dyn, bcast, flags);
+}
+
 __global__ void k_hhqr_plain(int m, int n, double* W, int ldw, double* tau, int* perm, DevState* st,
                              int gate_want)
 {
@@ -410,7 +429,7 @@ struct SingleLayout {
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
     L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
-    L_ALPH, L_COUNT
+    L_ALPH, L_BCAST, L_FLAGS, L_COUNT
 };
 static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
 
@@ -445,6 +464,8 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_PERM2] = sizeof(int) * n;
     sz[L_DSC] = sizeof(double) * n;
     sz[L_ALPH] = sizeof(double) * n;
+    sz[L_BCAST] = sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas);
+    sz[L_FLAGS] = sizeof(int) * n;
     SingleLayout L;
     size_t o = 0;
     for (int i = 0; i < L_COUNT; ++i) {
@@ -488,10 +509,35 @@ static int pick_w(int n, int mX, bool low, int sms, int forced)
     return std::max(p2, 1);
 }
 
+// Resident variant (owned columns in shared memory) when they fit, else the global one.
+// bcast: >= max(n, 2 * grid) * m doubles; flags: n ints (zeroed here for the plain QR).
 static int launch_hhqr(mpjsvd_ctx* h, bool pivot, int m, int n, double* W, int ldw, double* tau,
-                       int* perm, DevState* st, int gate_want)
+                       int* perm, DevState* st, int gate_want, double* bcast, int* flags)
 {
     int grid = std::max(1, std::min(n, std::min(h->num_sms, kMaxGroupCtas)));
+    size_t rsmem = hh_qr_res_smem_bytes(m, n, grid);
+    if (bcast && rsmem <= 200 * 1024) {
+        void* kern = pivot ? (void*)k_hhqr_res_piv : (void*)k_hhqr_res_plain;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+        if (e != cudaSuccess) return cuda_fail("hhqr_res smem attribute", e);
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kQrThreads, rsmem);
+        if (e != cudaSuccess) return cuda_fail("hhqr_res occupancy", e);
+        if (occ >= 1) {
+            if (pivot) {
+                void* args[] = {&m, &n, &W, &ldw, &tau, &perm, &st, &bcast};
+                e = cudaLaunchCooperativeKernel(kern, grid, kQrThreads, args, rsmem, h->stream);
+            } else {
+                e = cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n, h->stream);
+                if (e != cudaSuccess) return cuda_fail("hhqr_res flags", e);
+                void* args[] = {&m, &n, &W, &ldw, &tau, &perm, &st, &bcast, &flags, &gate_want};
+                e = cudaLaunchCooperativeKernel(kern, grid, kQrThreads, args, rsmem, h->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail("hhqr_res launch", e);
+            ++h->launch_count;
+            return 0;
+        }
+    }
     size_t smem = hh_qr_smem_bytes(m, n, grid);
     if (smem > 200 * 1024) return cuda_fail("hh_qr: too many rows", cudaErrorInvalidValue);
     void* kern = pivot ? (void*)k_hhqr_piv : (void*)k_hhqr_plain;
@@ -575,6 +621,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     int* perm2 = (int*)ptr(L_PERM2);
     void* dsc = ptr(L_DSC);
     void* alph = ptr(L_ALPH);
+    double* bcast = (double*)ptr(L_BCAST);
+    int* qflags = (int*)ptr(L_FLAGS);
     DevState* st = (DevState*)h->dstate;
     cudaStream_t s = h->stream;
     const int T256 = 256;
@@ -592,12 +640,12 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // ---- [3.1] QR preconditioning
     if (qr_first) {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, W0, m, st); ++h->launch_count;
-        if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1))) return rc;
+        if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1, bcast, qflags))) return rc;
         k_extract_upper<<<egrid, T256, 0, s>>>(n, W0, m, Wq, n); ++h->launch_count;
     } else {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, Wq, m, st); ++h->launch_count;
     }
-    if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1))) return rc;
+    if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1, bcast, qflags))) return rc;
     k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
     k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, X, P.precond); ++h->launch_count;
     record(h, 1);
@@ -651,7 +699,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);  // X^T upper when X lower
         g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
         if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
-        if ((rc = launch_hhqr(h, false, n, n, Bq, n, tau2, perm2, st, 1))) return rc;
+        if ((rc = launch_hhqr(h, false, n, n, Bq, n, tau2, perm2, st, 1, bcast, qflags))) return rc;
         k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
         if ((rc = launch_apply_q(h, n, n, n, Bq, n, tau2, Vacc, n, true, st, 1))) return rc;
         GemmArgs g2;
