@@ -347,6 +347,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         float* dscf = (float*)(slot + L.dsc);
         D.dsc = dscf;
         D.alph = slot + L.alph;
+        D.ver = nullptr;  // one CTA per matrix: visits run in order, no hand-off
         for (int j = tid; j < n; j += nthr) dscf[j] = 1.0f;
         __syncthreads();
         bool conv = false;
@@ -402,6 +403,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         double* dscd = (double*)(slot + L.dsc);
         D.dsc = dscd;
         D.alph = slot + L.alph;
+        D.ver = nullptr;  // one CTA per matrix: visits run in order, no hand-off
         for (int j = tid; j < n; j += nthr) dscd[j] = 1.0;
         __syncthreads();
         bool conv = false;

@@ -429,7 +429,7 @@ struct SingleLayout {
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
     L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
-    L_ALPH, L_BCAST, L_FLAGS, L_COUNT
+    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_COUNT
 };
 static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
 
@@ -466,6 +466,7 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_ALPH] = sizeof(double) * n;
     sz[L_BCAST] = sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas);
     sz[L_FLAGS] = sizeof(int) * n;
+    sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
     SingleLayout L;
     size_t o = 0;
     for (int i = 0; i < L_COUNT; ++i) {
@@ -482,12 +483,11 @@ static int sweep_blocks(int n, int w)
     return std::max(2, nb + (nb & 1));
 }
 
-static int even_ceil(int x) { return x <= 1 ? 1 : ((x + 1) & ~1); }
-
-// Block width of the sweeps. FP64 (work): just enough blocks to give every SM a visit per
-// round (the stage is FP64-throughput bound). FP32 (low): wide blocks (the stage is latency
-// bound: fewer rounds, fewer barriers). A visit keeps 2w columns x (mX / threads) rows in
-// registers, which caps w for tall X (<= 1024 threads, <= 32 doubles / 64 floats each).
+// Block width of the sweeps. FP64 (work): narrow blocks, so that enough visits run at once
+// for several CTAs per SM (the stage is FP64-throughput bound once latency is hidden).
+// FP32 (low): wide blocks (the stage is latency bound: fewer rounds). A visit keeps 2w
+// columns x (mX / threads) rows in registers, which caps w for tall X (<= 1024 threads,
+// <= 32 doubles / 64 floats each).
 static int pick_w(int n, int mX, bool low, int sms, int forced)
 {
     int wmax = low ? kWmaxLow : kWmaxWork;
@@ -499,8 +499,11 @@ static int pick_w(int n, int mX, bool low, int sms, int forced)
     } else if (low) {
         w = 8;
     } else {
-        w = even_ceil((n + 2 * sms - 1) / (2 * sms));
-        if (n <= 512) w = std::max(w, 8);
+        // narrowest power of two that still leaves >= 1.5 visits per SM in every round, so
+        // that two or more CTAs share each SM and hide each other's latency-bound steps
+        w = 1;
+        while ((double)n / (4.0 * w) >= 1.5 * sms) w *= 2;
+        if (n <= 512) w = std::max(w, 8);  // small n: latency bound, fewer rounds win
     }
     w = std::min(w, std::min(wmax, smem_cap));
     w = std::min(w, std::max(1, n / 2));
@@ -623,6 +626,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     void* alph = ptr(L_ALPH);
     double* bcast = (double*)ptr(L_BCAST);
     int* qflags = (int*)ptr(L_FLAGS);
+    unsigned* ver = (unsigned*)ptr(L_VER);
     DevState* st = (DevState*)h->dstate;
     cudaStream_t s = h->stream;
     const int T256 = 256;
@@ -685,7 +689,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         SweepDims Dl;
         Dl.n = n; Dl.mX = n; Dl.ldX = n; Dl.nV = 0; Dl.ldV = n; Dl.w = w_low;
         Dl.k = sweep_blocks(n, w_low); Dl.maxsweep = std::min(P.maxsweep, 64); Dl.tol = tol_low;
-        Dl.dsc = dsc; Dl.alph = alph;
+        Dl.dsc = dsc; Dl.alph = alph; Dl.ver = ver;
         if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
         k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
         k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
@@ -724,7 +728,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     SweepDims Dw;
     Dw.n = n; Dw.mX = n; Dw.ldX = n; Dw.nV = n; Dw.ldV = n; Dw.w = w_work;
     Dw.k = sweep_blocks(n, w_work); Dw.maxsweep = std::min(P.maxsweep, 64); Dw.tol = tol_work;
-    Dw.dsc = dsc; Dw.alph = alph;
+    Dw.dsc = dsc; Dw.alph = alph; Dw.ver = ver;
     if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
     record(h, 5);
 

@@ -13,7 +13,11 @@
 // gamma = x_p^T x_q, the pair is rotated when |gamma| > tol sqrt(alpha) sqrt(beta); then
 // zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)),
 // c = 1/sqrt(1 + t^2), x_p' = c (x_p - t x_q), x_q' = c (x_q + t x_p),
-// alpha' = alpha - t gamma, beta' = beta + t gamma.
+// alpha' = alpha - t gamma, beta' = beta + t gamma. The kernels evaluate the same t as
+// sign(zeta) 2|gamma| / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)) on operands
+// scaled by a power of two (rot_params): one reciprocal square root and one reciprocal
+// instead of two divisions and a square root, which matters because every binary64
+// operation on this chain costs a full FP64 pipe latency.
 //
 // Scaled ("fast") form. Each column is kept as x = d * xh with a scale d that persists
 // across visits (global arrays dsc, alph hold d and the tracked alpha of every column).
@@ -30,6 +34,13 @@
 // products of a round are combined by one multi-value warp reduction and W lanes of warp 0
 // compute the W rotations. Their parameters go to a dense per-round table; V's rows are
 // then streamed through registers and each thread replays the table on its rows.
+//
+// Scheduling (single-matrix path). Rounds are not separated by grid barriers: each block has
+// a version counter (the number of rounds that have finished with it), and a visit of round
+// R waits only until its two blocks have reached version R, i.e. until the two visits of
+// round R-1 that produced them have stored their columns. Several CTAs per SM then overlap
+// one visit's latency-bound steps (reductions, rotation parameters) with another visit's
+// FP64 arithmetic. One grid barrier per sweep decides convergence.
 #pragma once
 
 #include "common.cuh"
@@ -49,14 +60,72 @@ __host__ __device__ __forceinline__ constexpr void rr_pair(int k, int r, int i, 
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T rot_tangent(T alpha, T beta, T gamma)
+// 2^-e for the larger binary exponent e of |a| and |b| (clamped so the result is normal):
+// multiplying by it brings max(|a|, |b|) into [1, 2) exactly. Integer work only.
+__device__ __forceinline__ double pow2_down(double a, double b)
 {
-    T zeta = (beta - alpha) / (T(2) * gamma);
-    T az = fabs(zeta);
-    T big = sizeof(T) == 8 ? T(1e150) : T(1e18);
-    T t = (az > big) ? T(1) / (T(2) * az) : T(1) / (az + sqrt(T(1) + az * az));
-    return zeta >= T(0) ? t : -t;
+    int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
+    int e = min(max(max(ea, eb), 1), 2045);
+    return __hiloint2double((2046 - e) << 20, 0);
+}
+__device__ __forceinline__ float pow2_down(float a, float b)
+{
+    int ea = (__float_as_int(a) >> 23) & 0xff, eb = (__float_as_int(b) >> 23) & 0xff;
+    int e = min(max(max(ea, eb), 1), 253);
+    return __int_as_float((254 - e) << 23);
+}
+
+// Rotation of Section 2.1 for (alpha, beta, gamma), gamma != 0: t (the root of
+// t^2 + 2 zeta t - 1 = 0 with |t| <= 1, zeta = (beta - alpha) / (2 gamma); t > 0 when
+// zeta = 0), c = 1 / sqrt(1 + t^2) and 1 / c. With dd = beta - alpha, g2 = 2 gamma,
+// D = sqrt(dd^2 + g2^2) and S = |dd| + D: |t| = |g2| / S, sign(t) = sign(dd) sign(gamma).
+// t depends only on the ratio dd : g2, so both are first scaled by a power of two: no
+// intermediate overflows or underflows for any finite input.
+template <typename T>
+__device__ __forceinline__ void rot_params(T alpha, T beta, T gamma, T& t, T& c, T& ic)
+{
+    const T dd = beta - alpha, g2 = T(2) * gamma;
+    const T sc = pow2_down(dd, g2);
+    const T ds = dd * sc, gs = g2 * sc;
+    const T D2 = fma(ds, ds, gs * gs);
+    const T D = D2 * rsqrt(D2);
+    const T r = T(1) / (fabs(ds) + D);
+    const T num = (dd == T(0)) ? fabs(gs) : ((dd > T(0)) ? gs : -gs);
+    t = num * r;
+    const T q1 = fma(t, t, T(1));
+    c = rsqrt(q1);
+    ic = q1 * c;
+}
+
+// Sum of n >= 1 values with a dependency depth of about log2(4) + n / 4 instead of n.
+template <typename T>
+__device__ __forceinline__ T short_sum(const T* v, int n)
+{
+    T s0 = v[0], s1 = T(0), s2 = T(0), s3 = T(0);
+    if (n > 1) s1 = v[1];
+    if (n > 2) s2 = v[2];
+    if (n > 3) s3 = v[3];
+    int k = 4;
+    for (; k + 3 < n; k += 4) {
+        s0 += v[k];
+        s1 += v[k + 1];
+        s2 += v[k + 2];
+        s3 += v[k + 3];
+    }
+    for (; k < n; ++k) s0 += v[k];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Acquire load / release store of a version counter (cross-CTA hand-off of a block).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 struct SweepDims {
@@ -71,6 +140,7 @@ struct SweepDims {
     double tol;  // rotation threshold
     void* dsc;   // T[n]: column scales, 1 at the start of the stage
     void* alph;  // T[n]: tracked squared norms (true scale)
+    unsigned* ver;  // 2k block versions, X then V (cooperative single-matrix launch only)
 };
 
 constexpr int kMaxWarps = 32;
@@ -128,8 +198,7 @@ __device__ __forceinline__ void reg_norms(const T (&x)[RPT][2 * W], VisitShared<
     if ((lane & ((1 << sh) - 1)) == 0) sm.part[lane >> sh][wid] = acc[0];
     __syncthreads();
     if (tid < 2 * W) {
-        T s = T(0);
-        for (int k2 = 0; k2 < nw; ++k2) s += sm.part[tid][k2];
+        const T s = short_sum(sm.part[tid], nw);
         T dc = sm.d[tid];
         sm.alpha[tid] = (sm.gidx[tid] >= 0) ? s * dc * dc : T(0);
     }
@@ -161,19 +230,16 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
         const int a = pair_a<W>(intra, q, p), b = pair_b<W>(intra, q, p);
         unsigned act = 0;
         if (sm.gidx[a] >= 0 && sm.gidx[b] >= 0) {
-            T gh = T(0);
-            for (int k2 = 0; k2 < nw; ++k2) gh += sm.part[p][k2];
-            T da = sm.d[a], db = sm.d[b];
-            T gamma = gh * da * db;
-            T al = sm.alpha[a], be = sm.alpha[b];
-            if (gamma * gamma > tol * tol * al * be) {  // |gamma| > tol |x_a| |x_b|
-                T t = rot_tangent(al, be, gamma);
-                T q1 = T(1) + t * t;
-                T c = rsqrt(q1);  // cos of the rotation
-                T ic = q1 * c;    // 1 / c
-                T ia = sm.dinv[a], ib = sm.dinv[b];
-                sm.tab[slot][p] = t * db * ia;
-                sm.tba[slot][p] = t * da * ib;
+            const T gh = short_sum(sm.part[p], nw);
+            const T da = sm.d[a], db = sm.d[b];
+            const T ia = sm.dinv[a], ib = sm.dinv[b];
+            const T al = sm.alpha[a], be = sm.alpha[b];
+            const T gamma = gh * (da * db);
+            if (gamma * gamma > (tol * tol) * (al * be)) {  // |gamma| > tol |x_a| |x_b|
+                T t, c, ic;  // tangent, cosine and 1 / cosine of the rotation
+                rot_params(al, be, gamma, t, c, ic);
+                sm.tab[slot][p] = t * (db * ia);
+                sm.tba[slot][p] = t * (da * ib);
                 sm.d[a] = da * c;
                 sm.d[b] = db * c;
                 sm.dinv[a] = ia * ic;
@@ -216,9 +282,10 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
     }
 }
 
-// Replay the visit's rotation table on one row of V held in v[] (compile-time indices).
-template <int W, typename T>
-__device__ __forceinline__ void replay_row(double (&v)[2 * W], bool first, const VisitShared<T, W>& sm)
+// Replay the visit's rotation table on R rows of V held in v[][] (compile-time column
+// indices): rotations in table order, each applied to all R rows.
+template <int W, int R, typename T>
+__device__ __forceinline__ void replay_rows(double (&v)[R][2 * W], bool first, const VisitShared<T, W>& sm)
 {
     const int nintra = first ? W - 1 : 0;
 #pragma unroll
@@ -230,9 +297,12 @@ __device__ __forceinline__ void replay_row(double (&v)[2 * W], bool first, const
             if (!(m & (1u << p))) continue;
             const int a = pair_a<W>(true, q, p), b = pair_b<W>(true, q, p);
             const double ta = (double)sm.tab[q][p], tb = (double)sm.tba[q][p];
-            double va = v[a], vb = v[b];
-            v[a] = fma(-ta, vb, va);
-            v[b] = fma(tb, va, vb);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const double va = v[k][a], vb = v[k][b];
+                v[k][a] = fma(-ta, vb, va);
+                v[k][b] = fma(tb, va, vb);
+            }
         }
     }
 #pragma unroll
@@ -244,18 +314,23 @@ __device__ __forceinline__ void replay_row(double (&v)[2 * W], bool first, const
             if (!(m & (1u << p))) continue;
             const int a = pair_a<W>(false, q, p), b = pair_b<W>(false, q, p);
             const double ta = (double)sm.tab[slot][p], tb = (double)sm.tba[slot][p];
-            double va = v[a], vb = v[b];
-            v[a] = fma(-ta, vb, va);
-            v[b] = fma(tb, va, vb);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const double va = v[k][a], vb = v[k][b];
+                v[k][a] = fma(-ta, vb, va);
+                v[k][b] = fma(tb, va, vb);
+            }
         }
     }
 }
 
-// One visit of block pair (bi, bj): load to registers, rotate, store. Returns the rotation
-// count (all threads). All threads of the CTA must call it; mX <= RPT * blockDim.x.
+// X part of one visit of block pair (bi, bj): load to registers, rotate, store X, scales
+// and tracked norms. Returns the rotation count (all threads) and leaves the visit's rotation
+// table, fold factors and column indices in sm for replay_v. All threads of the CTA must
+// call it; mX <= RPT * blockDim.x.
 template <typename T, bool WITH_V, int W, int RPT>
-__device__ int jacobi_visit(const SweepDims& D, T* X, double* V, int bi, int bj, bool first,
-                            VisitShared<T, W>& sm)
+__device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool first,
+                              VisitShared<T, W>& sm)
 {
     const int tid = threadIdx.x, nthr = blockDim.x;
     constexpr int W2 = 2 * W;
@@ -334,31 +409,56 @@ __device__ int jacobi_visit(const SweepDims& D, T* X, double* V, int bi, int bj,
             dsc[sm.gidx[tid]] = sm.d[tid];
             alph[sm.gidx[tid]] = sm.alpha[tid];
         }
-        // ---- replay the rotations on the rows of V
-        if (WITH_V) {
-            for (int r = tid; r < D.nV; r += nthr) {
-                double v[W2];
-#pragma unroll
-                for (int c = 0; c < W2; ++c) {
-                    const int gc = sm.gidx[c];
-                    v[c] = (gc >= 0) ? __ldcg(V + cm(r, gc, D.ldV)) : 0.0;
-                }
-                replay_row<W, T>(v, first, sm);
-#pragma unroll
-                for (int c = 0; c < W2; ++c) {
-                    const int gc = sm.gidx[c];
-                    if (gc >= 0) {
-                        const double f = (double)sm.fold[c];
-                        V[cm(r, gc, D.ldV)] = (f == 1.0) ? v[c] : v[c] * f;
-                    }
-                }
-            }
-        }
     } else if (fresh) {
         // no rotation: only the recomputed norms change
         if (tid < W2 && sm.gidx[tid] >= 0) alph[sm.gidx[tid]] = sm.alpha[tid];
     }
     __syncthreads();
+    return nrot;
+}
+
+// Replay the rotation table of the last jacobi_visit_x (first: it had intra rounds) on the
+// rows of V, RPT rows per thread at a time: all loads of a pass are issued before the
+// first is used (one L2 round trip per pass instead of one per row). Ends synchronized.
+template <typename T, int W, int RPT>
+__device__ void replay_v(const SweepDims& D, double* V, bool first, const VisitShared<T, W>& sm)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    constexpr int W2 = 2 * W;
+    for (int r0 = tid; r0 < D.nV; r0 += RPT * nthr) {
+        double v[RPT][W2];
+#pragma unroll
+        for (int c = 0; c < W2; ++c) {
+            const int gc = sm.gidx[c];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = r0 + k * nthr;
+                v[k][c] = (gc >= 0 && r < D.nV) ? __ldcg(V + cm(r, gc, D.ldV)) : 0.0;
+            }
+        }
+        replay_rows<W, RPT, T>(v, first, sm);
+#pragma unroll
+        for (int c = 0; c < W2; ++c) {
+            const int gc = sm.gidx[c];
+            if (gc < 0) continue;
+            const double f = (double)sm.fold[c];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = r0 + k * nthr;
+                if (r < D.nV) V[cm(r, gc, D.ldV)] = (f == 1.0) ? v[k][c] : v[k][c] * f;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One whole visit: X part, then (with V and at least one rotation) the replay on V.
+template <typename T, bool WITH_V, int W, int RPT>
+__device__ int jacobi_visit(const SweepDims& D, T* X, double* V, int bi, int bj, bool first,
+                            VisitShared<T, W>& sm)
+{
+    const int nrot = jacobi_visit_x<T, WITH_V, W, RPT>(D, X, bi, bj, first, sm);
+    if (WITH_V && nrot > 0) replay_v<T, W, RPT>(D, V, first, sm);
     return nrot;
 }
 
@@ -389,6 +489,87 @@ __device__ int jacobi_sweeps(const Group& g, const SweepDims& D, T* X, double* V
         }
         unsigned long long total = __ldcg(&rot_sweep[sweep]);
         if (total == 0) {
+            *converged = true;
+            ++sweep;
+            break;
+        }
+    }
+    return sweep;
+}
+
+// Thread 0 waits (bounded) until blocks bi and bj have version >= R; false for every thread
+// if the wait gave up (MPJSVD_STATUS_TIMEOUT recorded) or the call failed elsewhere.
+__device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj, unsigned R, DevState* st)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u32(ver + bi) < R || ld_acquire_u32(ver + bj) < R) {
+            if ((++spins & 63u) == 0) {
+                if (call_failed(st)) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                    atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// jacobi_sweeps for a cooperative group of CTAs, scheduled by block versions instead of a
+// barrier per round. ver: 2k zeroed counters (X versions, then V versions). The visits of a sweep are numbered round-major
+// (f = r * k/2 + i) and CTA c takes f = c, c + G, ...: every visit waits only on visits with
+// smaller numbers, so the smallest unfinished one can always run (all CTAs are resident).
+template <typename T, bool WITH_V, int W, int RPT>
+__device__ int jacobi_sweeps_flow(const Group& g, const SweepDims& D, T* X, double* V,
+                                  unsigned long long* rot_sweep, unsigned* ver,
+                                  VisitShared<T, W>& sm, bool* converged)
+{
+    const int k = D.k, half = k / 2, rounds = k - 1;
+    const long long per_sweep = (long long)rounds * half;
+    int sweep = 0;
+    *converged = false;
+    for (; sweep < D.maxsweep; ++sweep) {
+        for (long long f = g.rank; f < per_sweep; f += g.size) {
+            const int r = (int)(f / half), i = (int)(f - (long long)r * half);
+            int bi, bj;
+            rr_pair(k, r, i, bi, bj);
+            if (bi > bj) { int t = bi; bi = bj; bj = t; }
+            const unsigned R = (unsigned)(sweep * rounds + r);
+            if (!wait_blocks(ver, bi, bj, R, g.st)) return -1;
+            const int nrot = jacobi_visit_x<T, WITH_V, W, RPT>(D, X, bi, bj, r == 0, sm);
+            // jacobi_visit_x ends with a CTA barrier: every store of X precedes the release,
+            // so the next round's visits of bi and bj can start while this CTA updates V
+            if (threadIdx.x == 0) {
+                if (nrot) atomicAdd(&rot_sweep[sweep], (unsigned long long)nrot);
+                __threadfence();
+                st_release_u32(ver + bi, R + 1);
+                st_release_u32(ver + bj, R + 1);
+            }
+            if (WITH_V) {
+                // V has its own versions (ver + k): replays of a block stay in round order
+                unsigned* vv = ver + k;
+                if (!wait_blocks(vv, bi, bj, R, g.st)) return -1;
+                if (nrot > 0) replay_v<T, W, RPT>(D, V, r == 0, sm);
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release_u32(vv + bi, R + 1);
+                    st_release_u32(vv + bj, R + 1);
+                }
+            }
+        }
+        if (!g.sync()) return -1;
+        if (__ldcg(&rot_sweep[sweep]) == 0) {
             *converged = true;
             ++sweep;
             break;

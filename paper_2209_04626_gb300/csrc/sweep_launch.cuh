@@ -25,12 +25,13 @@ __global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, 
     if (call_failed(st)) return;
     if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
     Group g{(int)blockIdx.x, (int)gridDim.x, st};
-    // persistent scales start at 1
+    // persistent scales start at 1, block versions at 0
     T* dsc = (T*)D.dsc;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += gridDim.x * blockDim.x) dsc[j] = T(1);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 2 * D.k; b += gridDim.x * blockDim.x) D.ver[b] = 0u;
     if (!g.sync()) return;
     bool conv = false;
-    int sweeps = jacobi_sweeps<T, WITH_V, W, RPT>(g, D, X, V, st->rot_sweep[phase], sm, &conv);
+    int sweeps = jacobi_sweeps_flow<T, WITH_V, W, RPT>(g, D, X, V, st->rot_sweep[phase], D.ver, sm, &conv);
     if (sweeps < 0) return;
     fold_scales_cols<T>(g, D.mX, D.n, X, D.ldX, WITH_V ? D.nV : 0, WITH_V ? V : nullptr, D.ldV, dsc);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
