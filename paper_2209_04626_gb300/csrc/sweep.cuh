@@ -97,6 +97,51 @@ __device__ __forceinline__ void rot_params(T alpha, T beta, T gamma, T& t, T& c,
     ic = q1 * c;
 }
 
+// gamma / dd for the rare case below (not inlined: keeps the division off the common path).
+static __device__ __noinline__ double ratio_slow(double gamma, double dd) { return gamma / dd; }
+
+// binary64 variant: t is evaluated in binary32 from the scaled operands and then used exactly
+// as a binary64 number. The transformation [c, c t; -c t, c] is orthogonal to binary64
+// precision for ANY t as long as c = 1 / sqrt(1 + t^2) is accurate for that t, which is
+// computed in binary64; only how completely the pair is annihilated (to ~2^-23 of gamma)
+// depends on t, and the next sweep removes the remainder. The binary32 chain is about a
+// fifth as long as the binary64 one (each binary64 operation costs a full FP64 pipe
+// latency on this part). If the scaled gamma underflows binary32 (|gamma| < 2^-126 |dd|),
+// t = gamma / dd is taken in binary64.
+template <>
+__device__ __forceinline__ void rot_params<double>(double alpha, double beta, double gamma, double& t,
+                                                   double& c, double& ic)
+{
+    const double dd = beta - alpha;
+    const double sc = pow2_down(dd, gamma);
+    const float ds = (float)(dd * sc), gs = 2.0f * (float)(gamma * sc);
+    const float D2 = fmaf(ds, ds, gs * gs);
+    const float D = D2 * rsqrtf(D2);
+    const float num = (ds == 0.0f) ? fabsf(gs) : ((ds > 0.0f) ? gs : -gs);
+    const float tf = __fdividef(num, fabsf(ds) + D);
+    t = (double)tf;
+    if (tf == 0.0f) t = ratio_slow(gamma, dd);
+    const double q1 = fma(t, t, 1.0);
+    c = rsqrt(q1);
+    ic = q1 * c;
+}
+
+// True when x <= 0 or x < y / 16 up to a factor of two (y > 0), from the sign and binary
+// exponents (no floating-point instruction): flags a tracked norm that lost about four bits
+// to cancellation.
+__device__ __forceinline__ bool lost_bits(double x, double y)
+{
+    const int hx = __double2hiint(x);
+    if (hx <= 0) return true;  // negative, zero, or far below any normal y
+    return ((hx >> 20) & 0x7ff) + 4 < ((__double2hiint(y) >> 20) & 0x7ff);
+}
+__device__ __forceinline__ bool lost_bits(float x, float y)
+{
+    const int bx = __float_as_int(x);
+    if (bx <= 0) return true;  // negative or zero
+    return ((bx >> 23) & 0xff) + 4 < ((__float_as_int(y) >> 23) & 0xff);
+}
+
 // Sum of n >= 1 values with a dependency depth of about log2(4) + n / 4 instead of n.
 template <typename T>
 __device__ __forceinline__ T short_sum(const T* v, int n)
@@ -208,7 +253,7 @@ __device__ __forceinline__ void reg_norms(const T (&x)[RPT][2 * W], VisitShared<
 // One inner round (pairs given by intra/q), slot = its index in the visit's table.
 template <typename T, bool WITH_V, int W, int RPT>
 __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int q, int slot,
-                                            VisitShared<T, W>& sm, T tol)
+                                            VisitShared<T, W>& sm, T tol2)
 {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int SH = 5 - ilog2c(W);
@@ -235,7 +280,7 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
             const T ia = sm.dinv[a], ib = sm.dinv[b];
             const T al = sm.alpha[a], be = sm.alpha[b];
             const T gamma = gh * (da * db);
-            if (gamma * gamma > (tol * tol) * (al * be)) {  // |gamma| > tol |x_a| |x_b|
+            if (gamma * gamma > tol2 * (al * be)) {  // |gamma| > tol |x_a| |x_b|
                 T t, c, ic;  // tangent, cosine and 1 / cosine of the rotation
                 rot_params(al, be, gamma, t, c, ic);
                 sm.tab[slot][p] = t * (db * ia);
@@ -244,8 +289,8 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
                 sm.d[b] = db * c;
                 sm.dinv[a] = ia * ic;
                 sm.dinv[b] = ib * ic;
-                T na = al - t * gamma, nb = be + t * gamma;
-                if (na < T(0.0625) * al || nb < T(0.0625) * be) sm.flags[1] = 1;
+                const T na = fma(-t, gamma, al), nb = fma(t, gamma, be);
+                if (lost_bits(na, al) || lost_bits(nb, be)) sm.flags[1] = 1;
                 sm.alpha[a] = na;
                 sm.alpha[b] = nb;
                 act = 1u << p;
@@ -334,7 +379,7 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
 {
     const int tid = threadIdx.x, nthr = blockDim.x;
     constexpr int W2 = 2 * W;
-    const T tol = T(D.tol);
+    const T tol2 = T(D.tol * D.tol);  // the rotation test compares squares
     T* dsc = (T*)D.dsc;
     T* alph = (T*)D.alph;
     // fold a column into its data once its scale is this small (persistent scales only
@@ -379,11 +424,11 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
     // ---- inner rounds (unrolled: compile-time column indices)
     if (first) {
 #pragma unroll
-        for (int q = 0; q < W - 1; ++q) inner_round<T, WITH_V, W, RPT>(x, true, q, q, sm, tol);
+        for (int q = 0; q < W - 1; ++q) inner_round<T, WITH_V, W, RPT>(x, true, q, q, sm, tol2);
     }
     const int base = first ? W - 1 : 0;
 #pragma unroll
-    for (int q = 0; q < W; ++q) inner_round<T, WITH_V, W, RPT>(x, false, q, base + q, sm, tol);
+    for (int q = 0; q < W; ++q) inner_round<T, WITH_V, W, RPT>(x, false, q, base + q, sm, tol2);
 
     const int nrot = sm.flags[0];
     if (nrot > 0) {

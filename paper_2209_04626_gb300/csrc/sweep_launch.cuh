@@ -57,7 +57,9 @@ static int launch_sweeps_wr(mpjsvd_ctx* h, const SweepDims& D0, T* X, double* V,
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
     if (e != cudaSuccess) return cuda_fail("sweep occupancy", e);
     if (occ < 1) return cuda_fail("sweep occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
-    int grid = std::min(D.k / 2, occ * h->num_sms);
+    // up to two CTAs per visit of a round: consecutive rounds of a visit index go to different
+    // CTAs, so a CTA's replay on V overlaps the next round's work on X
+    int grid = std::min(D.k, occ * h->num_sms);
     grid = std::max(1, std::min(grid, 1024));
     void* args[] = {&D, &X, &V, &st, &phase, &gate_want};
     e = cudaLaunchCooperativeKernel((void*)kern, grid, threads, args, 0, h->stream);
