@@ -164,6 +164,24 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
 int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S, double* V,
                        double tol, void* cuda_stream);
 
+/* Householder QR of one matrix, in place (the QR preconditioning of Section 3.1 and the QR
+ * of the precision switch of Section 3.3 as a standalone call; blocked, compact-WY form).
+ *   m, n : 1 <= n <= m <= 12480, n <= 12288
+ *   A    : device, m x n, leading dimension lda >= m; on return R on and above the
+ *          diagonal and the tails of the reflectors below it (LAPACK geqrf layout)
+ *   tau  : device, n output; H_j = I - tau_j v_j v_j^T with v_j(j) = 1, Q = H_0 ... H_{n-1}
+ * Reflector convention: beta = -sign(alpha) |x| (alpha = the diagonal entry, sign(0) = +),
+ * tail = x(j+1:) / (alpha - beta), tau = (beta - alpha) / beta; tau = 0 and v = e_j when
+ * the tail is zero. Stream-ordered on the handle's stream; uses the handle's workspace. */
+int mpjsvd_geqrf(mpjsvd_handle h, int m, int n, double* A, int lda, double* tau);
+
+/* C <- Q C with Q = H_0 ... H_{k-1} from mpjsvd_geqrf (A: m x k reflectors, lda >= m; tau: k).
+ *   C : device, m x ncols, leading dimension ldc >= m, overwritten
+ * 1 <= k <= m <= 12480, 1 <= ncols <= 12288. Forming the thin Q is this call applied to the
+ * first ncols columns of the identity. */
+int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, int lda,
+                   const double* tau, double* C, int ldc);
+
 /* Synchronize the handle's stream and copy the stats of the last mpjsvd_svd call. */
 int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st);
 

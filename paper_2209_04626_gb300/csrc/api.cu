@@ -103,6 +103,14 @@ int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream)
     c->have_events = true;
     for (int i = 0; i < 8; ++i)
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
+    c->have_side = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 5 && c->have_side; ++i)
+        if (cudaEventCreateWithFlags(&c->qev[i], cudaEventDisableTiming) != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(c->qev[k]);
+            cudaStreamDestroy(c->side);
+            c->have_side = false;
+        }
+    cudaGetLastError();  // a failed optional resource leaves no sticky error behind
     *h = c;
     return 0;
 }
@@ -181,6 +189,32 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
     return svd_backward(h, m, n, U, S, V, gU, gS, gV, gA, gap_tol, n_flagged);
 }
 
+int mpjsvd_geqrf(mpjsvd_handle h, int m, int n, double* A, int lda, double* tau)
+{
+    if (!h) return -1;
+    if (m < 1 || m < n || m > 12480 || mpj::bqr_nb(m) == 0) return -2;
+    if (n < 1 || n > 12288) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (!tau) return -6;
+    return mpj::qr_call(h, m, n, A, lda, tau);
+}
+
+int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, int lda,
+                   const double* tau, double* C, int ldc)
+{
+    if (!h) return -1;
+    if (m < 1 || m > 12480) return -2;
+    if (ncols < 1 || ncols > 12288) return -3;
+    if (k < 1 || k > m) return -4;
+    if (!A) return -5;
+    if (lda < m) return -6;
+    if (!tau) return -7;
+    if (!C) return -8;
+    if (ldc < m) return -9;
+    return mpj::apply_q_call(h, m, ncols, k, A, lda, tau, C, ldc);
+}
+
 int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st)
 {
     if (!h) return -1;
@@ -196,6 +230,11 @@ int mpjsvd_destroy(mpjsvd_handle h)
     if (h->bws) cudaFree(h->bws);
     if (h->aws) cudaFree(h->aws);
     if (h->dstate) cudaFree(h->dstate);
+    if (h->have_side) {
+        cudaStreamSynchronize(h->side);
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(h->qev[i]);
+        cudaStreamDestroy(h->side);
+    }
     if (h->have_events)
         for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
     delete h;

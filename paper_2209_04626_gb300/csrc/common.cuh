@@ -41,6 +41,7 @@ struct DevState {
     double maxnorm;        // max column norm of X (branch test)
     unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
+    unsigned wy_count[2];                  // blocked QR: Gram tiles finished, per stream
 };
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative

@@ -30,6 +30,10 @@ struct mpjsvd_ctx {
     bool last_valid;
     int last_block_w_low, last_block_w_work;
     int launch_count;  // kernels launched by the last call
+    // second stream for the blocked QR's look-ahead (fork/join through events on `stream`)
+    cudaStream_t side;
+    cudaEvent_t qev[5];  // [0] panel done, [1..3] wide updates (ring), [4] join
+    bool have_side;
 };
 
 namespace mpj {
@@ -49,6 +53,18 @@ int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st,
                       int gate_want, int* threads_out);
 int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
                       int phase, int gate_want, int* threads_out);
+
+// blocked Householder QR and compact-WY application of Q (qr_blocked.cu)
+int bqr_nb(int m);                       // panel width for m rows; 0: use the unblocked kernels
+size_t bqr_wbuf_doubles(int ncols_max);  // scratch for bqr_factor / bqr_apply
+int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
+               int gate_want);
+int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,
+              double* C, int ldc, bool ident, double* W, DevState* st, int gate_want);
+// standalone calls behind mpjsvd_geqrf / mpjsvd_apply_q (workspace and state of the handle)
+int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau);
+int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int lda, const double* tau,
+                 double* C, int ldc);
 
 // single-matrix pipeline (svd_single.cu)
 int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U, double* S,

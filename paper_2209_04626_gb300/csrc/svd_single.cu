@@ -429,7 +429,7 @@ struct SingleLayout {
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
     L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
-    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_COUNT
+    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_WY, L_COUNT
 };
 static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
 
@@ -467,12 +467,21 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_BCAST] = sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas);
     sz[L_FLAGS] = sizeof(int) * n;
     sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
+    sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n);
+    // The QRCP's broadcast slots are live only during the QR preconditioning; the buffers
+    // from X up to V_acc are first written after it, so the slots share their memory when
+    // they fit (L_BITS, zeroed at the start of a call, is not in that span).
+    size_t span = 0;
+    for (int i = L_X; i < L_SIG; ++i) span += align256(sz[i] ? sz[i] : 16);
+    const bool alias_bcast = sz[L_BCAST] <= span;
+    if (alias_bcast) sz[L_BCAST] = 0;
     SingleLayout L;
     size_t o = 0;
     for (int i = 0; i < L_COUNT; ++i) {
         L.off[i] = o;
         o += align256(sz[i] ? sz[i] : 16);
     }
+    if (alias_bcast) L.off[L_BCAST] = L.off[L_X];
     L.total = o;
     return L;
 }
@@ -627,6 +636,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     double* bcast = (double*)ptr(L_BCAST);
     int* qflags = (int*)ptr(L_FLAGS);
     unsigned* ver = (unsigned*)ptr(L_VER);
+    double* wy = (double*)ptr(L_WY);
+    // n x n factorizations are always blocked (every n <= 12288 has a panel width); the QRCP's
+    // broadcast slots may alias the stage buffers, so no unblocked kernel runs after it
+    if (bqr_nb(n) == 0) return cuda_fail("blocked QR: no panel width for n", cudaErrorInvalidValue);
+    const bool blocked_m = bqr_nb(m) > 0 && m <= 12480;
     DevState* st = (DevState*)h->dstate;
     cudaStream_t s = h->stream;
     const int T256 = 256;
@@ -644,7 +658,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // ---- [3.1] QR preconditioning
     if (qr_first) {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, W0, m, st); ++h->launch_count;
-        if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1, bcast, qflags))) return rc;
+        if (blocked_m) {
+            if ((rc = bqr_factor(h, m, n, W0, m, tau0, wy, st, -1))) return rc;
+        } else {
+            if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1, bcast, qflags))) return rc;
+        }
         k_extract_upper<<<egrid, T256, 0, s>>>(n, W0, m, Wq, n); ++h->launch_count;
     } else {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, Wq, m, st); ++h->launch_count;
@@ -703,9 +721,9 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);  // X^T upper when X lower
         g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
         if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
-        if ((rc = launch_hhqr(h, false, n, n, Bq, n, tau2, perm2, st, 1, bcast, qflags))) return rc;
+        if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
         k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
-        if ((rc = launch_apply_q(h, n, n, n, Bq, n, tau2, Vacc, n, true, st, 1))) return rc;
+        if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
         GemmArgs g2;
         g2.M = n; g2.N = n; g2.K = n;
         g2.A = X; g2.lda = n; g2.transA = false;
@@ -739,8 +757,14 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("finalize kernels", e);
     if (qr_first) {
-        if ((rc = launch_apply_q(h, n, n, n, WqL, n, tau, U, m, false, st, -1))) return rc;
-        if ((rc = launch_apply_q(h, m, n, n, W0, m, tau0, U, m, false, st, -1))) return rc;
+        if ((rc = bqr_apply(h, n, n, n, WqL, n, tau, U, m, false, wy, st, -1))) return rc;
+        if (blocked_m) {
+            if ((rc = bqr_apply(h, m, n, n, W0, m, tau0, U, m, false, wy, st, -1))) return rc;
+        } else {
+            if ((rc = launch_apply_q(h, m, n, n, W0, m, tau0, U, m, false, st, -1))) return rc;
+        }
+    } else if (blocked_m) {
+        if ((rc = bqr_apply(h, m, n, n, WqL, m, tau, U, m, false, wy, st, -1))) return rc;
     } else {
         if ((rc = launch_apply_q(h, m, n, n, WqL, m, tau, U, m, false, st, -1))) return rc;
     }

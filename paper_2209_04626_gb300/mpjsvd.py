@@ -23,7 +23,8 @@ STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2
 
 EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsvd_set_params",
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
-           "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc"]
+           "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
+           "mpjsvd_apply_q"]
 
 
 class Params(ctypes.Structure):
@@ -76,6 +77,8 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_destroy.argtypes = [_vp]
     L.mpjsvd_last_error.restype = ctypes.c_char_p
     L.mpjsvd_svd_noalloc.argtypes = [_i, _i, _vp, _i, _vp, _vp, _vp, _d, _vp]
+    L.mpjsvd_geqrf.argtypes = [_vp, _i, _i, _vp, _i, _vp]
+    L.mpjsvd_apply_q.argtypes = [_vp, _i, _i, _i, _vp, _i, _vp, _vp, _i]
     _lib = L
     return L
 
@@ -154,6 +157,14 @@ def mpjsvd_svd_noalloc(m, n, A_ptr, lda, U_ptr, S_ptr, V_ptr, tol=0.0, stream=No
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     return load_library().mpjsvd_svd_noalloc(m, n, _vp(A_ptr), lda, _vp(U_ptr), _vp(S_ptr),
                                              _vp(V_ptr), tol, _vp(s))
+
+
+def mpjsvd_geqrf(h, m, n, A_ptr, lda, tau_ptr):
+    return load_library().mpjsvd_geqrf(h, m, n, _vp(A_ptr), lda, _vp(tau_ptr))
+
+
+def mpjsvd_apply_q(h, m, ncols, k, A_ptr, lda, tau_ptr, C_ptr, ldc):
+    return load_library().mpjsvd_apply_q(h, m, ncols, k, _vp(A_ptr), lda, _vp(tau_ptr), _vp(C_ptr), ldc)
 
 
 # ---------------------------------------------------------------- conveniences
@@ -236,6 +247,25 @@ class Handle:
 
     def stats(self):
         return mpjsvd_get_stats(self.h)
+
+    def geqrf(self, A):
+        """Householder QR of a CUDA float64 (m, n) tensor: returns (QR in geqrf layout, tau)."""
+        A = colmajor(A, A.device)  # a fresh column-major copy (factorized in place)
+        m, n = A.shape
+        tau = torch.empty(n, dtype=torch.float64, device=A.device)
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(A.device).cuda_stream)
+        _check(mpjsvd_geqrf(self.h, m, n, A.data_ptr(), A.stride(1), tau.data_ptr()), "mpjsvd_geqrf")
+        return A, tau
+
+    def apply_q(self, QR, tau, C):
+        """Q C for Q from geqrf (QR: (m, k) reflectors, tau: k); returns a new tensor."""
+        C = colmajor(C, C.device)  # a fresh column-major copy (overwritten)
+        m, nc = C.shape
+        k = tau.shape[0]
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(C.device).cuda_stream)
+        _check(mpjsvd_apply_q(self.h, m, nc, k, QR.data_ptr(), QR.stride(1), tau.data_ptr(),
+                              C.data_ptr(), C.stride(1)), "mpjsvd_apply_q")
+        return C
 
     def backward(self, U, S, V, gU=None, gS=None, gV=None, gap_tol=1e-3):
         m, n = U.shape

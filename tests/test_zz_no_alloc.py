@@ -42,6 +42,15 @@ def _handle(A):
     return U, S, V
 
 
+def test_noalloc_at_its_maximum_size():
+    rng = np.random.default_rng(32)
+    A = inputs.known_sigma(rng, 512, 256, np.logspace(0, -4, 256))
+    U, S, V = _noalloc(A)
+    Ur, Sr, Vr = _handle(A)
+    check_factorization(A, U, S, V)
+    assert np.max(np.abs(S - Sr) / Sr) <= 1e-12
+
+
 def test_noalloc_matches_handle_path_on_two_calls_in_a_row():
     rng = np.random.default_rng(31)
     cases = [inputs.known_sigma(rng, 300, 200, np.logspace(0, -5, 200)),
