@@ -33,7 +33,7 @@ class _Variant:
         class Params(ctypes.Structure):
             _fields_ = [("tol_alg", creal), ("tol_orth", creal), ("tol_cond_coef", creal),
                         ("trailing_frac", creal), ("tol", creal), ("maxsweep", ctypes.c_int),
-                        ("mode", ctypes.c_int), ("precond", ctypes.c_int)]
+                        ("mode", ctypes.c_int), ("precond", ctypes.c_int), ("qrcp", ctypes.c_int)]
 
         class Stats(ctypes.Structure):
             _fields_ = [("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
@@ -53,6 +53,8 @@ class _Variant:
         L.orc_house.argtypes = [ctypes.c_int, rp, rp]
         L.orc_geqrf.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp]
         L.orc_geqp3.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, _ip, rp]
+        L.orc_geqp3_mixed.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, _ip, rp]
+        L.orc_qrcp_pivots_f32.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, _ip]
         L.orc_apply_q.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, rp,
                                   ctypes.c_int, rp, rp, ctypes.c_int]
         L.orc_apply_q.restype = None
@@ -139,6 +141,30 @@ def geqp3(A, ext=False):
     rc = v.L.orc_geqp3(m, n, v.ptr(A), max(1, m), jpvt.ctypes.data_as(_ip), v.ptr(tau))
     assert rc == 0
     return A, jpvt[:n], tau[:min(m, n)]
+
+
+def geqp3_mixed(A, ext=False):
+    """Alg. 5: binary32 pivot search on lower(A), then the QR of A P in working precision.
+    Returns (QR of A P in geqrf layout, jpvt, tau)."""
+    v = _v(ext)
+    A = v.arr(A).copy(order="F")
+    m, n = A.shape
+    tau = np.zeros(max(1, min(m, n)), dtype=v.np)
+    jpvt = np.zeros(max(1, n), dtype=np.int32)
+    rc = v.L.orc_geqp3_mixed(m, n, v.ptr(A), max(1, m), jpvt.ctypes.data_as(_ip), v.ptr(tau))
+    assert rc == 0
+    return A, jpvt[:n], tau[:min(m, n)]
+
+
+def qrcp_pivots_f32(A, ext=False):
+    """The binary32 column permutation of Alg. 5 (step 2) for A."""
+    v = _v(ext)
+    A = v.arr(A).copy(order="F")
+    m, n = A.shape
+    jpvt = np.zeros(max(1, n), dtype=np.int32)
+    rc = v.L.orc_qrcp_pivots_f32(m, n, v.ptr(A), max(1, m), jpvt.ctypes.data_as(_ip))
+    assert rc == 0
+    return jpvt[:n]
 
 
 def apply_q(QR, tau, C, trans=False, ext=False):

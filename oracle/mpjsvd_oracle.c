@@ -40,6 +40,7 @@ void orc_default_params(orc_params* p)
     p->maxsweep = 30;
     p->mode = 0;
     p->precond = 0;
+    p->qrcp = 0;
 }
 
 static orc_real nrm2(int len, const orc_real* x)
@@ -146,6 +147,128 @@ int orc_geqp3(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau)
     free(vn1);
     free(vn2);
     return 0;
+}
+
+/* |x| in binary32 without underflow or overflow of the squares: the entries are first scaled
+ * by the power of two that brings max |x_i| into [1, 2) (exact), as single-precision LAPACK
+ * norms avoid underflow. */
+static float nrm2_f32(int len, const float* x)
+{
+    float amax = 0.0f;
+    for (int i = 0; i < len; ++i) {
+        float a = fabsf(x[i]);
+        if (a > amax) amax = a;
+    }
+    if (amax == 0.0f) return 0.0f;
+    int e;
+    frexpf(amax, &e);
+    const float sc = ldexpf(1.0f, 1 - e);
+    float s = 0.0f;
+    for (int i = 0; i < len; ++i) {
+        float y = x[i] * sc;
+        s += y * y;
+    }
+    return sqrtf(s) / sc;
+}
+
+/* Alg. 5, step 2 in binary32: the same Businger-Golub steps as orc_geqp3 (first maximum on
+ * ties, norm downdating with recomputation when the downdate keeps less than half of the
+ * binary32 digits), on lower(A); only the permutation is kept. Norms use nrm2_f32. */
+int orc_qrcp_pivots_f32(int m, int n, const orc_real* A, int lda, int* jpvt)
+{
+    if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
+    /* lower(A): scale by 2^-e, e the binary exponent of max |a_ij| (exact in binary64) */
+    orc_real amax = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) {
+            orc_real a = RFABS(AT(A, i, j, lda));
+            if (a > amax) amax = a;
+        }
+    int e = 0;
+    if (amax > 0.0) frexp((double)amax, &e); /* amax = f 2^e, f in [0.5, 1) */
+    const double scale = ldexp(1.0, 1 - e);   /* amax * scale in [1, 2) */
+    float* L = (float*)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
+    float* vn1 = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* vn2 = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* v = (float*)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1));
+    if (!L || !vn1 || !vn2 || !v) { free(L); free(vn1); free(vn2); free(v); return -9; }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) L[(size_t)j * m + i] = (float)((double)AT(A, i, j, lda) * scale);
+    const float tol3z = sqrtf(5.9604644775390625e-08f); /* sqrt(2^-24) */
+    for (int c = 0; c < n; ++c) {
+        jpvt[c] = c;
+        vn1[c] = nrm2_f32(m, &L[(size_t)c * m]);
+        vn2[c] = vn1[c];
+    }
+    int k = m < n ? m : n;
+    for (int j = 0; j < k; ++j) {
+        int p = j;
+        for (int c = j + 1; c < n; ++c)
+            if (vn1[c] > vn1[p]) p = c;
+        if (p != j) {
+            for (int i = 0; i < m; ++i) {
+                float t = L[(size_t)j * m + i];
+                L[(size_t)j * m + i] = L[(size_t)p * m + i];
+                L[(size_t)p * m + i] = t;
+            }
+            int ti = jpvt[j]; jpvt[j] = jpvt[p]; jpvt[p] = ti;
+            vn1[p] = vn1[j];
+            vn2[p] = vn2[j];
+        }
+        /* Householder reflector of L(j:m, j), the same convention as orc_house */
+        float* colj = &L[(size_t)j * m];
+        float alpha = colj[j], tj = 0.0f;
+        const float tailn = (j + 1 < m) ? nrm2_f32(m - j - 1, &colj[j + 1]) : 0.0f;
+        if (tailn != 0.0f) {
+            float nrm = nrm2_f32(m - j, &colj[j]);
+            float beta = (alpha >= 0.0f) ? -nrm : nrm;
+            tj = (beta - alpha) / beta;
+            float den = alpha - beta;
+            v[j] = 1.0f;
+            for (int i = j + 1; i < m; ++i) v[i] = colj[i] / den;
+            colj[j] = beta;
+            for (int i = j + 1; i < m; ++i) colj[i] = v[i];
+        }
+        for (int c = j + 1; c < n; ++c) {
+            float* col = &L[(size_t)c * m];
+            if (tj != 0.0f) {
+                float w = col[j];
+                for (int i = j + 1; i < m; ++i) w += v[i] * col[i];
+                w *= tj;
+                col[j] -= w;
+                for (int i = j + 1; i < m; ++i) col[i] -= w * v[i];
+            }
+            if (vn1[c] != 0.0f) {
+                float r = fabsf(col[j]) / vn1[c];
+                float t = 1.0f - r * r;
+                if (t < 0.0f) t = 0.0f;
+                float q = vn1[c] / vn2[c];
+                if (t * q * q <= tol3z) {
+                    vn1[c] = (j + 1 < m) ? nrm2_f32(m - j - 1, &col[j + 1]) : 0.0f;
+                    vn2[c] = vn1[c];
+                } else {
+                    vn1[c] *= sqrtf(t);
+                }
+            }
+        }
+    }
+    free(L); free(vn1); free(vn2); free(v);
+    return 0;
+}
+
+/* Alg. 5: pivots from binary32, then the QR of A P in working precision. */
+int orc_geqp3_mixed(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau)
+{
+    int rc = orc_qrcp_pivots_f32(m, n, A, lda, jpvt);
+    if (rc) return rc;
+    orc_real* T = (orc_real*)malloc(sizeof(orc_real) * (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
+    if (!T) return -9;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) T[(size_t)j * m + i] = AT(A, i, jpvt[j], lda);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) AT(A, i, j, lda) = T[(size_t)j * m + i];
+    free(T);
+    return orc_geqrf(m, n, A, lda, tau);
 }
 
 void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
@@ -337,7 +460,8 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
             for (int i = 0; i < n; ++i) AT(R, i, j, n) = AT(W0, i, j, m);
     }
     /* QR preconditioning: A1 P = Q1 R; X = R^T (default) or X = R (Q2 = I). */
-    orc_geqp3(n, n, R, n, jpvt, tau1);
+    if (p.qrcp == 1) orc_geqp3_mixed(n, n, R, n, jpvt, tau1);
+    else orc_geqp3(n, n, R, n, jpvt, tau1);
     for (int j = 0; j < n; ++j)
         for (int i = 0; i <= j; ++i) {
             if (p.precond == 1) AT(X, i, j, n) = AT(R, i, j, n);

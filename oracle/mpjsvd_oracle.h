@@ -42,6 +42,9 @@ typedef struct {
     int precond;           /* Jacobi input after the QRCP A1 P = Q1 R: 0 -> X = R^T (lower
                               triangular; SVD of R with the roles of U and V exchanged),
                               1 -> X = R (Alg. 4 with Q2 = I) */
+    int qrcp;              /* the RRQR of the preconditioning: 0 -> Businger-Golub in working
+                              precision (orc_geqp3), 1 -> the mixed-precision RRQR of Alg. 5
+                              (orc_geqp3_mixed) */
 } orc_params;
 
 /* What the driver did (per call). */
@@ -74,6 +77,17 @@ int orc_geqrf(int m, int n, orc_real* A, int lda, orc_real* tau);
  * jpvt[i] = original index of the column in position i (0-based). Column norms are
  * downdated after each step and recomputed when cancellation is severe. */
 int orc_geqp3(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau);
+
+/* Mixed-precision RRQR (Alg. 5): the column permutation of a Businger-Golub QRCP of lower(A)
+ * computed in binary32 (lower(A) = A scaled by the power of two that brings max |a_ij| into
+ * [1, 2), so that binary32 neither overflows nor loses the small columns to underflow first),
+ * then the Householder QR of A P in working precision. On return A holds that QR of A P
+ * (orc_geqrf layout, columns in pivot order), jpvt[j] = the column of A in position j. */
+int orc_geqp3_mixed(int m, int n, orc_real* A, int lda, int* jpvt, orc_real* tau);
+
+/* Only the binary32 pivot search of Alg. 5 (step 2): jpvt from the scaled lower(A). A is not
+ * modified. */
+int orc_qrcp_pivots_f32(int m, int n, const orc_real* A, int lda, int* jpvt);
 
 /* C <- Q C (trans = 0) or Q^T C (trans = 1), Q = H_0 H_1 ... H_{k-1} from orc_geqrf /
  * orc_geqp3 output (V, ldv, tau). C is m x ncols. */

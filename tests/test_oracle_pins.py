@@ -204,6 +204,72 @@ def test_geqp3_matches_lapack_pivots():
     assert err.max() < 25 * U64 * 16
 
 
+# ---------------------------------------------------------------- Alg. 5 (mixed-precision RRQR)
+
+def test_mixed_rrqr_pivots_match_binary64_when_unambiguous():
+    # strongly graded columns (ratio 10 between neighbours in norm): the pivot order is decided
+    # by margins far above binary32 rounding, so Alg. 5's pivots equal the binary64 QRCP's
+    rng = np.random.default_rng(41)
+    n = 30
+    A = rng.standard_normal((60, n)) * (10.0 ** -np.arange(n))[rng.permutation(n)]
+    jp32 = oracle.qrcp_pivots_f32(A)
+    _, jp64, _ = oracle.geqp3(A)
+    assert np.array_equal(jp32, jp64)
+    QRm, jpm, taum = oracle.geqp3_mixed(A)
+    QR64, _, tau64 = oracle.geqp3(A)
+    assert np.array_equal(jpm, jp64)
+    scale = np.abs(np.diag(QR64[:n]))
+    assert np.all(np.abs(np.triu(QRm[:n]) - np.triu(QR64[:n])).max(axis=1) <= 1e-13 * np.abs(A).max() * 8)
+
+
+def test_mixed_rrqr_is_rank_revealing_to_binary32_accuracy():
+    # at every step the chosen column had the largest remaining norm, up to binary32 rounding:
+    # |R_jj| >= (1 - 1e-4) max_{k >= j} |R(j:, k)| with R the binary64 QR of A P
+    rng = np.random.default_rng(42)
+    m, n = 120, 70
+    A = inputs.known_sigma(rng, m, n, np.logspace(0, -6, n)) * rng.uniform(0.2, 5.0, n)
+    QR, jpvt, tau = oracle.geqp3_mixed(A)
+    assert sorted(jpvt.tolist()) == list(range(n))
+    R = np.triu(QR[:n])
+    for j in range(n):
+        rem = np.linalg.norm(R[j:, j:], axis=0)
+        assert abs(R[j, j]) >= (1 - 1e-4) * rem.max()
+    # the factorization is of A P
+    Q = oracle.apply_q(QR, tau, np.eye(m)[:, :n])
+    assert np.abs(Q @ R - A[:, jpvt]).max() <= 1e-14 * np.abs(A).max() * 16
+
+
+def test_mixed_rrqr_ties_keep_the_first_column_and_scaling_is_exact():
+    # exactly equal norms at every step (scaled unit columns: each reflector is the identity):
+    # the first maximum wins every time
+    E = 3.0 * np.eye(40)[:, :12]
+    assert np.array_equal(oracle.qrcp_pivots_f32(E), np.arange(12))
+    # two identical columns of the largest norm: the lower index goes first
+    rng = np.random.default_rng(43)
+    B = rng.standard_normal((40, 6)) * np.array([1.0, 0.5, 0.25, 0.1, 0.05, 0.01])
+    B = np.column_stack([B[:, 1:4], B[:, 0], B[:, 4:], B[:, 0]])  # copies of column 0 at 3 and 6
+    assert oracle.qrcp_pivots_f32(B)[0] == 3
+    # the power-of-two scaling of lower(A) keeps binary32 in range: huge and tiny matrices
+    # pivot exactly like the unscaled one
+    rng = np.random.default_rng(44)
+    A = rng.standard_normal((50, 20)) * np.logspace(0, -3, 20)
+    jp = oracle.qrcp_pivots_f32(A)
+    assert np.array_equal(oracle.qrcp_pivots_f32(A * 2.0 ** 900), jp)
+    assert np.array_equal(oracle.qrcp_pivots_f32(A * 2.0 ** -1000), jp)
+
+
+def test_svd_with_mixed_rrqr_matches_lapack():
+    rng = np.random.default_rng(45)
+    m, n = 90, 60
+    A = inputs.known_sigma(rng, m, n, np.logspace(0, -3, n))
+    for mode in ("mixed", "plain"):
+        U, S, V, st = oracle.svd(A, mode=mode, qrcp=1)
+        assert st["status"] == 0
+        s_lapack = np.linalg.svd(A, compute_uv=False)
+        assert np.max(np.abs(S - s_lapack) / s_lapack) < 1e-12
+        assert np.abs((U * S) @ V.T - A).max() < 1e-13 * np.abs(A).max() * 10
+
+
 # ---------------------------------------------------------------- Alg. 1 in both precisions
 
 def test_jacobi_f64_and_f32_converge_to_svd():
