@@ -55,6 +55,11 @@ extern "C" {
 #define MPJSVD_PRECOND_RT 0  /* Jacobi on X = R^T (lower triangular); default */
 #define MPJSVD_PRECOND_R 1   /* Jacobi on X = R (Alg. 4 with Q2 = I) */
 
+/* params.qrcp: the rank-revealing QR of the preconditioning (Section 3.1). */
+#define MPJSVD_QRCP_MIXED 0  /* Alg. 5: binary32 pivot search on lower(A), binary64 QR of A P;
+                                default */
+#define MPJSVD_QRCP_F64 1    /* Businger-Golub QR with column pivoting in binary64 */
+
 typedef struct mpjsvd_ctx* mpjsvd_handle;
 
 /* Tunables. Defaults (mpjsvd_default_params) are the paper's values of Section 7.1. */
@@ -71,6 +76,8 @@ typedef struct {
     int qr_first;         /* 1: plain QR of A before the QRCP when m > n (Alg. 4 lines 1-3);
                              0 (default): QRCP applied to A directly (same R and P) */
     int timing;           /* 1: record per-phase CUDA-event times in mpjsvd_stats */
+    int qrcp;             /* MPJSVD_QRCP_*; Alg. 5 falls back to binary64 when the binary32
+                             matrix does not fit the resident kernel (stats.qrcp tells) */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
@@ -93,6 +100,7 @@ typedef struct {
     float ms_work;
     float ms_final;
     int launches;         /* CUDA kernels the call launched (gated-off stages included) */
+    int qrcp;             /* the RRQR that ran: MPJSVD_QRCP_MIXED or MPJSVD_QRCP_F64 */
 } mpjsvd_stats;
 
 /* Fill *p with the defaults. Returns 0, or -1 if p is NULL. */
@@ -108,7 +116,9 @@ int mpjsvd_set_params(mpjsvd_handle h, const mpjsvd_params* p);
 
 /* Thin SVD of one matrix (Algorithm 4).
  *   m, n : 1 <= n <= m <= 24576, n <= 12288
- *   A    : device, m x n, leading dimension lda >= m; not modified
+ *   A    : device, m x n, leading dimension lda >= m; not modified. Entries must be finite
+ *          (else MPJSVD_STATUS_NONFINITE) and their squares summed over a column must not
+ *          overflow binary64 (|a_ij| well below 1e154; column norms are not pre-scaled)
  *   U    : device, m x n output, leading dimension m
  *   S    : device, n output, descending
  *   V    : device, n x n output, leading dimension n
@@ -174,6 +184,18 @@ int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double
  * tail = x(j+1:) / (alpha - beta), tau = (beta - alpha) / beta; tau = 0 and v = e_j when
  * the tail is zero. Stream-ordered on the handle's stream; uses the handle's workspace. */
 int mpjsvd_geqrf(mpjsvd_handle h, int m, int n, double* A, int lda, double* tau);
+
+/* The rank-revealing QR of the preconditioning (Section 3.1; Alg. 5 by default, see
+ * params.qrcp) as a standalone call: A P = Q R.
+ *   m, n : 1 <= n <= m <= 24576, n <= 12288
+ *   A    : device, m x n, lda >= m; on return the Householder QR of A P in pivot order
+ *          (mpjsvd_geqrf layout: R on and above the diagonal, reflector tails below)
+ *   jpvt : device, n output: column j of A P is column jpvt[j] of A
+ *   tau  : device, n output
+ * Alg. 5: jpvt from a Businger-Golub pivot search in binary32 on A scaled by a power of two,
+ * then the binary64 QR of A P; MPJSVD_QRCP_F64: Businger-Golub in binary64 throughout (the
+ * first maximum of the downdated norms wins in both). stats.qrcp records which ran. */
+int mpjsvd_geqp3(mpjsvd_handle h, int m, int n, double* A, int lda, int* jpvt, double* tau);
 
 /* C <- Q C with Q = H_0 ... H_{k-1} from mpjsvd_geqrf (A: m x k reflectors, lda >= m; tau: k).
  *   C : device, m x ncols, leading dimension ldc >= m, overwritten

@@ -65,6 +65,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->precond = MPJSVD_PRECOND_RT;
     p->qr_first = 0;
     p->timing = 0;
+    p->qrcp = MPJSVD_QRCP_MIXED;
     return 0;
 }
 
@@ -74,6 +75,7 @@ static int check_params(const mpjsvd_params* p)
     if (p->block_w < 0 || p->block_w > 16) return 1;
     if (p->mode < 0 || p->mode > 2) return 1;
     if (p->precond < 0 || p->precond > 1) return 1;
+    if (p->qrcp < 0 || p->qrcp > 1) return 1;
     if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
     return 0;
 }
@@ -198,6 +200,18 @@ int mpjsvd_geqrf(mpjsvd_handle h, int m, int n, double* A, int lda, double* tau)
     if (lda < m) return -5;
     if (!tau) return -6;
     return mpj::qr_call(h, m, n, A, lda, tau);
+}
+
+int mpjsvd_geqp3(mpjsvd_handle h, int m, int n, double* A, int lda, int* jpvt, double* tau)
+{
+    if (!h) return -1;
+    if (m < 1 || m < n || m > 24576) return -2;
+    if (n < 1 || n > 12288) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (!jpvt) return -6;
+    if (!tau) return -7;
+    return mpj::geqp3_call(h, m, n, A, lda, jpvt, tau);
 }
 
 int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, int lda,

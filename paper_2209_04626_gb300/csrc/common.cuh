@@ -42,6 +42,8 @@ struct DevState {
     unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
     unsigned wy_count[2];                  // blocked QR: Gram tiles finished, per stream
+    unsigned long long amax_bits;          // Alg. 5: max |a_ij| (bits of a non-negative double)
+    float4 cand_sc[512];                   // Alg. 5: candidate's (alpha, |tail|, |col|) x parity
 };
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative
@@ -52,35 +54,48 @@ __device__ __forceinline__ bool call_failed(const DevState* st)
             (MPJSVD_STATUS_NONFINITE | MPJSVD_STATUS_TIMEOUT)) != 0;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Bounded grid barrier for a cooperative launch (all CTAs co-resident). Returns false
 // if the wait timed out or another CTA reported an error; callers then exit.
+// Thread 0 arrives with an acq_rel atomic (after the CTA barrier, so the release covers every
+// thread's earlier writes); the last arrival resets the count and releases the next
+// generation; the others spin on an acquire load of the generation (no sleep: the wait is
+// usually well under a microsecond), checking the time limit every 1024 polls.
 __device__ __forceinline__ bool grid_sync(DevState* st)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int* vgen = &st->bar_gen;
-        unsigned int gen = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        const unsigned gen = ld_acquire_gpu(&st->bar_gen);
+        unsigned arrived;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&st->bar_count) : "memory");
         if (arrived == gridDim.x - 1) {
             st->bar_count = 0;
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&st->bar_gen), "r"(gen + 1) : "memory");
         } else {
-            uint64_t t0 = globaltimer_ns();
-            unsigned int spins = 0;
-            while (*vgen == gen) {
-                if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kSpinLimitNs) {
-                    atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
-                    ok = 0;
-                    break;
+            const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire_gpu(&st->bar_gen) == gen) {
+                if ((++spins & 1023u) == 0) {
+                    if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                        atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) {
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
         if (*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) ok = 0;
         s_ok = ok;
     }

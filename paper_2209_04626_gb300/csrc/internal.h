@@ -30,6 +30,7 @@ struct mpjsvd_ctx {
     bool last_valid;
     int last_block_w_low, last_block_w_work;
     int launch_count;  // kernels launched by the last call
+    int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
     // second stream for the blocked QR's look-ahead (fork/join through events on `stream`)
     cudaStream_t side;
     cudaEvent_t qev[5];  // [0] panel done, [1..3] wide updates (ring), [4] join
@@ -61,6 +62,10 @@ int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, dou
                int gate_want);
 int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,
               double* C, int ldc, bool ident, double* W, DevState* st, int gate_want);
+// binary32 pivot search of Alg. 5 (qrcp_low.cu); 1 = does not fit, nothing launched
+int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
+                    DevState* st);
+
 // standalone calls behind mpjsvd_geqrf / mpjsvd_apply_q (workspace and state of the handle)
 int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau);
 int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int lda, const double* tau,
@@ -70,6 +75,7 @@ int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int ld
 int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U, double* S,
                double* V, double tol);
 int read_stats(mpjsvd_ctx* h, mpjsvd_stats* st);
+int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, double* tau);
 
 // batched pipeline (svd_batched.cu)
 int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,

@@ -1,0 +1,507 @@
+// qrcp_low.cu -- the binary32 pivot search of the mixed-precision RRQR (Alg. 5, step 2).
+//
+// lower(A) is A scaled by the power of two that brings max |a_ij| into [1, 2) and rounded to
+// binary32; a Businger-Golub QR with column pivoting of lower(A) then yields the permutation P
+// (the binary32 R is discarded; the binary64 QR of A P follows in qr_blocked.cu). Same steps
+// as the binary64 kernel: the first maximum of the downdated norms wins, the norms are
+// downdated by the new row entry and recomputed when the downdate keeps less than half of
+// the binary32 digits. Every norm is taken on power-of-two scaled entries, so the squares of
+// small columns do not underflow (the convention of single-precision LAPACK norms).
+//
+// One cooperative launch; CTA r owns the columns r, r + G, ... resident in shared memory.
+// Each step publishes every CTA's candidate (norm, column) and the candidate's rows in one
+// slot, then one grid barrier: every CTA then reads the winner's column from its slot.
+#include "common.cuh"
+#include "internal.h"
+#include "qr.cuh"
+
+namespace mpj {
+
+constexpr int kLowThreads = 256;
+constexpr int kLowBatch = 4;
+
+__device__ __forceinline__ float block_max_f(float v, float* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float r = (lane < nw) ? red[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    return r;
+}
+
+// |x(lo:m)| of a shared-memory column without underflow or overflow of the squares.
+__device__ float norm_scaled(const float* x, int lo, int m, float* red)
+{
+    float a = 0.0f;
+    for (int i = lo + threadIdx.x; i < m; i += blockDim.x) a = fmaxf(a, fabsf(x[i]));
+    a = block_max_f(a, red);
+    if (a == 0.0f) return 0.0f;
+    const int eb = (__float_as_int(a) >> 23) & 0xff;
+    const float sc = __int_as_float((254 - eb) << 23);  // a * sc in [1, 2)
+    float s = 0.0f;
+    for (int i = lo + threadIdx.x; i < m; i += blockDim.x) {
+        const float y = x[i] * sc;
+        s = fmaf(y, y, s);
+    }
+    s = block_sum(s, red);
+    return sqrtf(s) / sc;
+}
+
+__host__ __device__ inline size_t qrcp_low_smem_bytes(int m, int n, int gsize)
+{
+    const int own = (n + gsize - 1) / gsize;
+    return sizeof(float) * ((size_t)own * m + m + 3 * (size_t)own) + sizeof(int) * own;
+}
+
+__global__ void __launch_bounds__(kLowThreads)
+    k_qrcp_low(int m, int n, const double* __restrict__ A, int lda, int* perm, float* bcast,
+               DevState* st)
+{
+    extern __shared__ float lsm[];
+    __shared__ float red[kLowBatch * 33];
+    __shared__ double s_amax;
+    __shared__ int s_piv, s_src, s_recompute;
+    if (call_failed(st)) return;
+    const Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    const int own = (n - g.rank + g.size - 1) / g.size;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    float* C = lsm;                     // own x m
+    float* vs = C + (size_t)own * m;    // m: the step's column, then its reflector
+    float* vn1 = vs + m;
+    float* vn2 = vn1 + own;
+    float* rowj = vn2 + own;
+    int* act = (int*)(rowj + own);
+    const float tol3z = 2.44140625e-04f;  // sqrt(2^-24)
+
+    // ---- lower(A): global max |a_ij| (non-negative doubles order like their bit patterns)
+    double am = 0.0;
+    for (int t = 0; t < own; ++t) {
+        const double* src = A + cm(0, g.rank + t * g.size, lda);
+        for (int i = tid; i < m; i += nthr) am = fmax(am, fabs(src[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if (lane == 0) atomicMax(&st->amax_bits, (unsigned long long)__double_as_longlong(am));
+    if (!g.sync()) return;
+    if (tid == 0) s_amax = __longlong_as_double((long long)__ldcg(&st->amax_bits));
+    __syncthreads();
+    const double amax = s_amax;
+    const int eb = (__double2hiint(amax) >> 20) & 0x7ff;
+    const double scale = (amax > 0.0) ? __hiloint2double((2046 - min(max(eb, 1), 2045)) << 20, 0) : 1.0;
+    for (int t = 0; t < own; ++t) {
+        const double* src = A + cm(0, g.rank + t * g.size, lda);
+        float* dst = C + (size_t)t * m;
+        for (int i = tid; i < m; i += nthr) dst[i] = (float)(src[i] * scale);
+    }
+    for (int t = tid; t < own; t += nthr) act[t] = 1;
+    __syncthreads();
+    for (int t = 0; t < own; ++t) {
+        const float v = norm_scaled(C + (size_t)t * m, 0, m, red);
+        if (tid == 0) { vn1[t] = v; vn2[t] = v; }
+    }
+    __syncthreads();
+
+    const int k = min(m, n);
+    for (int j = 0; j < k; ++j) {
+        // ---- candidate of this CTA (first maximum in column order), published with its rows
+        if (tid < 32) {
+            int best = -1;
+            float bv = 0.0f;
+            for (int t = lane; t < own; t += 32) {
+                if (!act[t]) continue;
+                if (best < 0 || vn1[t] > bv) { bv = vn1[t]; best = t; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                if (ob >= 0 && (best < 0 || ov > bv || (ov == bv && ob < best))) { bv = ov; best = ob; }
+            }
+            if (lane == 0) {
+                put_candidate(st, j & 1, g.rank, (double)bv, best >= 0 ? g.rank + best * g.size : -1);
+                s_src = best;
+            }
+        }
+        __syncthreads();
+        if (s_src >= 0) {
+            const float* c = C + (size_t)s_src * m;
+            float* slot = bcast + ((size_t)(j & 1) * g.size + g.rank) * m;
+            for (int i = j + tid; i < m; i += nthr) slot[i] = c[i];
+        }
+        if (!g.sync()) return;
+        if (tid < 32) {
+            const int best = pivot_argmax(st, j & 1, g.size, lane);
+            if (lane == 0) s_piv = best;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p < 0 || p >= n) {
+            if (tid == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+            return;
+        }
+        const float* src = bcast + ((size_t)(j & 1) * g.size + (p % g.size)) * m;
+        for (int i = j + tid; i < m; i += nthr) vs[i] = __ldcg(src + i);
+        __syncthreads();
+
+        // ---- reflector of the pivot column (the convention of the binary64 kernels)
+        float tj = 0.0f;
+        const float tailn = norm_scaled(vs, j + 1, m, red);
+        if (tailn != 0.0f) {
+            const float alpha = vs[j];
+            const float nrm = norm_scaled(vs, j, m, red);
+            const float beta = (alpha >= 0.0f) ? -nrm : nrm;
+            tj = (beta - alpha) / beta;
+            const float den = alpha - beta;
+            __syncthreads();
+            for (int i = j + 1 + tid; i < m; i += nthr) vs[i] = vs[i] / den;
+        }
+        __syncthreads();
+        const bool mine = (p % g.size == g.rank);
+        const int tp = (p - g.rank) / g.size;
+
+        // ---- apply it to the other active columns, downdate their norms
+        int t = 0;
+        while (true) {
+            float* cols[kLowBatch];
+            int tix[kLowBatch];
+            int nb = 0;
+            for (; t < own && nb < kLowBatch; ++t) {
+                if (act[t] && !(mine && t == tp)) {
+                    tix[nb] = t;
+                    cols[nb] = C + (size_t)t * m;
+                    ++nb;
+                }
+            }
+            if (nb == 0) break;
+            for (int b = nb; b < kLowBatch; ++b) { cols[b] = cols[0]; tix[b] = tix[0]; }
+            if (tj != 0.0f) {
+                float acc[kLowBatch], w[kLowBatch];
+#pragma unroll
+                for (int b = 0; b < kLowBatch; ++b) acc[b] = 0.0f;
+                for (int i = j + 1 + tid; i < m; i += nthr) {
+                    const float vi = vs[i];
+#pragma unroll
+                    for (int b = 0; b < kLowBatch; ++b) acc[b] = fmaf(vi, cols[b][i], acc[b]);
+                }
+                block_sum_multi<kLowBatch>(acc, red, w);
+#pragma unroll
+                for (int b = 0; b < kLowBatch; ++b) w[b] = tj * (cols[b][j] + w[b]);
+                __syncthreads();  // every thread has read c_j before it changes
+                if (tid == 0)
+                    for (int b = 0; b < nb; ++b) cols[b][j] -= w[b];
+                for (int i = j + 1 + tid; i < m; i += nthr) {
+                    const float vi = vs[i];
+#pragma unroll
+                    for (int b = 0; b < kLowBatch; ++b)
+                        if (b < nb) cols[b][i] = fmaf(-w[b], vi, cols[b][i]);
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                s_recompute = 0;
+                for (int b = 0; b < nb; ++b) rowj[tix[b]] = cols[b][j];
+            }
+            __syncthreads();
+            if (tid < nb) {
+                const int tt = tix[tid];
+                const float v1 = vn1[tt];
+                if (v1 != 0.0f) {
+                    const float r = fabsf(rowj[tt]) / v1;
+                    float q = 1.0f - r * r;
+                    q = q < 0.0f ? 0.0f : q;
+                    const float ratio = v1 / vn2[tt];
+                    if (q * ratio * ratio <= tol3z) atomicOr(&s_recompute, 1 << tid);
+                    else vn1[tt] = v1 * sqrtf(q);
+                }
+            }
+            __syncthreads();
+            const int mask = s_recompute;
+            for (int b = 0; b < nb; ++b) {
+                if (!(mask & (1 << b))) continue;
+                const float v = norm_scaled(cols[b], j + 1, m, red);
+                if (tid == 0) { vn1[tix[b]] = v; vn2[tix[b]] = v; }
+            }
+            __syncthreads();
+        }
+        if (mine && tid == 0) {
+            act[tp] = 0;
+            perm[j] = p;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Register-resident variant: warp w of CTA b owns column c = 8 b + w, its rows lane + 32 k
+// (k < KR) in registers, so applying a reflector is warp-local (no CTA barrier). Before each
+// grid barrier the CTA's candidate warp publishes its rows j.. and the reflector's scalars
+// (alpha, |tail|, |column|, computed exactly from its registers), so after the barrier every
+// CTA has the step's reflector without a reduction. Same pivot rule, downdating and norms as
+// the kernel above.
+constexpr int kRegWarps = 8;
+
+// Phase probes of the register-resident kernel: empty here; a profiling build may define them.
+#ifndef MPJ_QRCP_PROBE_BEGIN
+#define MPJ_QRCP_PROBE_BEGIN
+#define MPJ_QRCP_PROBE(i)
+#define MPJ_QRCP_PROBE_END
+#endif
+
+template <int KR>
+__device__ __forceinline__ float reg_norm_scaled(const float (&x)[KR], int lo, int lane)
+{
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        if (lane + 32 * k >= lo) a = fmaxf(a, fabsf(x[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if (a == 0.0f) return 0.0f;
+    const int eb = (__float_as_int(a) >> 23) & 0xff;
+    const float sc = __int_as_float((254 - eb) << 23);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        if (lane + 32 * k >= lo) {
+            const float y = x[k] * sc;
+            s = fmaf(y, y, s);
+        }
+    s = warp_sum(s);
+    return sqrtf(s) / sc;
+}
+
+// the entry of row r (all lanes receive it)
+template <int KR>
+__device__ __forceinline__ float reg_row(const float (&x)[KR], int r, int lane)
+{
+    float v = 0.0f;
+    const int kr = r >> 5;
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        if (k == kr) v = x[k];
+    return __shfl_sync(0xffffffffu, v, r & 31);
+}
+
+template <int KR>
+__global__ void __launch_bounds__(kRegWarps * 32)
+    k_qrcp_low_reg(int m, int n, const double* __restrict__ A, int lda, int* perm, float* bcast,
+                   DevState* st)
+{
+    __shared__ float vs[32 * KR];
+    __shared__ float wvn[kRegWarps];
+    __shared__ int wcol[kRegWarps];
+    __shared__ double s_amax;
+    __shared__ int s_piv;
+    __shared__ float4 s_sc;
+    if (call_failed(st)) return;
+    const Group g{(int)blockIdx.x, (int)gridDim.x, st};
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int c = blockIdx.x * kRegWarps + wid;  // this warp's column
+    bool act = c < n;
+    const float tol3z = 2.44140625e-04f;  // sqrt(2^-24)
+
+    // ---- lower(A): global max |a_ij|, then the scaled binary32 column in registers
+    double am = 0.0;
+    if (act)
+        for (int i = lane; i < m; i += 32) am = fmax(am, fabs(A[cm(i, c, lda)]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if (lane == 0) atomicMax(&st->amax_bits, (unsigned long long)__double_as_longlong(am));
+    if (!g.sync()) return;
+    if (tid == 0) s_amax = __longlong_as_double((long long)__ldcg(&st->amax_bits));
+    __syncthreads();
+    const double amax = s_amax;
+    const int eb = (__double2hiint(amax) >> 20) & 0x7ff;
+    const double scale = (amax > 0.0) ? __hiloint2double((2046 - min(max(eb, 1), 2045)) << 20, 0) : 1.0;
+    float x[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const int i = lane + 32 * k;
+        x[k] = (act && i < m) ? (float)(A[cm(i, c, lda)] * scale) : 0.0f;
+    }
+    float vn1 = act ? reg_norm_scaled<KR>(x, 0, lane) : 0.0f;
+    float vn2 = vn1;
+    MPJ_QRCP_PROBE_BEGIN
+
+    const int kmax = min(m, n);
+    for (int j = 0; j < kmax; ++j) {
+        // ---- this CTA's candidate (first maximum in column order) publishes itself
+        if (lane == 0) {
+            wvn[wid] = act ? vn1 : -1.0f;
+            wcol[wid] = act ? c : -1;
+        }
+        __syncthreads();
+        MPJ_QRCP_PROBE(0)
+        int cw = -1;
+        float cv = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kRegWarps; ++w)
+            if (wcol[w] >= 0 && (cw < 0 || wvn[w] > cv)) { cv = wvn[w]; cw = w; }
+        if (wid == cw) {
+            float* slot = bcast + ((size_t)(j & 1) * g.size + g.rank) * m;
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                const int i = lane + 32 * k;
+                if (i >= j && i < m) slot[i] = x[k];
+            }
+            const float alpha = reg_row<KR>(x, j, lane);
+            const float tailn = reg_norm_scaled<KR>(x, j + 1, lane);
+            const float nrm = reg_norm_scaled<KR>(x, j, lane);
+            if (lane == 0) {
+                put_candidate(st, j & 1, g.rank, (double)cv, c);
+                st->cand_sc[(j & 1) * kQrSlotStride + g.rank] = make_float4(alpha, tailn, nrm, 0.0f);
+            }
+        } else if (cw < 0 && tid == 0) {
+            put_candidate(st, j & 1, g.rank, 0.0, -1);
+        }
+        MPJ_QRCP_PROBE(1)
+        if (!g.sync()) return;
+        MPJ_QRCP_PROBE(2)
+        if (wid == 0) {
+            // argmax over the candidates with every CTA's scalars loaded in the same pass
+            constexpr int K = kQrSlotStride / 32;
+            double2 cd[K];
+            float4 sc[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const int r = lane + 32 * q;
+                cd[q] = (r < g.size) ? __ldcg(&st->cand[(j & 1) * kQrSlotStride + r]) : make_double2(0.0, -1.0);
+                sc[q] = (r < g.size) ? __ldcg(&st->cand_sc[(j & 1) * kQrSlotStride + r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            int best = -1;
+            double bv = 0.0;
+            float4 bs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const int idx = (int)cd[q].y;
+                if (idx >= 0 && (best < 0 || cd[q].x > bv || (cd[q].x == bv && idx < best))) {
+                    bv = cd[q].x; best = idx; bs = sc[q];
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, best, o);
+                const float ox = __shfl_xor_sync(0xffffffffu, bs.x, o);
+                const float oy = __shfl_xor_sync(0xffffffffu, bs.y, o);
+                const float oz = __shfl_xor_sync(0xffffffffu, bs.z, o);
+                if (oi >= 0 && (best < 0 || ov > bv || (ov == bv && oi < best))) {
+                    bv = ov; best = oi; bs = make_float4(ox, oy, oz, 0.f);
+                }
+            }
+            if (lane == 0) {
+                s_piv = best;
+                s_sc = bs;
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p < 0 || p >= n) {
+            if (tid == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+            return;
+        }
+        MPJ_QRCP_PROBE(3)
+        const int pb = p / kRegWarps;  // the winner's CTA
+        const float alpha = s_sc.x, tailn = s_sc.y, nrm = s_sc.z;
+        float tj = 0.0f, den = 1.0f;
+        if (tailn != 0.0f) {
+            const float beta = (alpha >= 0.0f) ? -nrm : nrm;
+            tj = (beta - alpha) / beta;
+            den = alpha - beta;
+        }
+        const float* src = bcast + ((size_t)(j & 1) * g.size + pb) * m;
+        if (tj != 0.0f)
+            for (int i = j + 1 + tid; i < m; i += blockDim.x) vs[i] = __ldcg(src + i) / den;
+        __syncthreads();
+        MPJ_QRCP_PROBE(4)
+
+        // ---- apply H_j to this warp's column, downdate its norm
+        if (act && c == p) {
+            act = false;
+            if (lane == 0) perm[j] = p;
+        } else if (act) {
+            if (tj != 0.0f) {
+                float d = 0.0f;
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i > j && i < m) d = fmaf(vs[i], x[k], d);
+                }
+                d = warp_sum(d);
+                const float w = tj * (reg_row<KR>(x, j, lane) + d);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i > j && i < m) x[k] = fmaf(-w, vs[i], x[k]);
+                    else if (i == j) x[k] -= w;
+                }
+            }
+            if (vn1 != 0.0f) {
+                const float r = fabsf(reg_row<KR>(x, j, lane)) / vn1;
+                float q = 1.0f - r * r;
+                q = q < 0.0f ? 0.0f : q;
+                const float ratio = vn1 / vn2;
+                if (q * ratio * ratio <= tol3z) {
+                    vn1 = reg_norm_scaled<KR>(x, j + 1, lane);
+                    vn2 = vn1;
+                } else {
+                    vn1 = vn1 * sqrtf(q);
+                }
+            }
+        }
+        MPJ_QRCP_PROBE(5)
+        __syncthreads();  // wvn / wcol and vs are rewritten by the next step
+        MPJ_QRCP_PROBE(6)
+    }
+    MPJ_QRCP_PROBE_END
+}
+
+template <int KR>
+static int launch_reg(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
+                      DevState* st)
+{
+    const int grid = (n + kRegWarps - 1) / kRegWarps;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qrcp_low_reg<KR>, kRegWarps * 32, 0);
+    if (e != cudaSuccess) return cuda_fail("qrcp_low_reg occupancy", e);
+    if (grid > kQrSlotStride || grid > occ * h->num_sms) return 1;
+    void* args[] = {&m, &n, &A, &lda, &perm, &bcast, &st};
+    e = cudaLaunchCooperativeKernel((void*)k_qrcp_low_reg<KR>, grid, kRegWarps * 32, args, 0, h->stream);
+    if (e != cudaSuccess) return cuda_fail("qrcp_low_reg launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+// Launch the binary32 pivot search: register-resident when a column fits a warp's registers
+// and there is a warp per column, else columns resident in shared memory; returns 1
+// (nothing launched) when neither fits, so the caller takes the binary64 QRCP instead.
+int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
+                    DevState* st)
+{
+    int rc = 1;
+    if (m <= 256) rc = launch_reg<8>(h, m, n, A, lda, perm, bcast, st);
+    else if (m <= 512) rc = launch_reg<16>(h, m, n, A, lda, perm, bcast, st);
+    else if (m <= 1024) rc = launch_reg<32>(h, m, n, A, lda, perm, bcast, st);
+    else if (m <= 2048) rc = launch_reg<64>(h, m, n, A, lda, perm, bcast, st);  // 216 registers
+    if (rc <= 0) return rc;
+    const int grid = std::max(1, std::min(n, std::min(h->num_sms, kQrSlotStride)));
+    const size_t smem = qrcp_low_smem_bytes(m, n, grid);
+    if (smem > 200 * 1024) return 1;
+    cudaError_t e = cudaFuncSetAttribute(k_qrcp_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("qrcp_low smem attribute", e);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qrcp_low, kLowThreads, smem);
+    if (e != cudaSuccess) return cuda_fail("qrcp_low occupancy", e);
+    if (occ < 1) return 1;
+    void* args[] = {&m, &n, &A, &lda, &perm, &bcast, &st};
+    e = cudaLaunchCooperativeKernel((void*)k_qrcp_low, grid, kLowThreads, args, smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail("qrcp_low launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+}  // namespace mpj

@@ -667,8 +667,23 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     } else {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, Wq, m, st); ++h->launch_count;
     }
-    if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1, bcast, qflags))) return rc;
-    k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
+    // RRQR: Alg. 5 (binary32 pivots, then the blocked binary64 QR of A P in pivot order) or
+    // the binary64 Businger-Golub kernel (reflectors gathered into pivot order afterwards)
+    bool mixed_done = false;
+    if (P.qrcp == MPJSVD_QRCP_MIXED && bqr_nb(mq) > 0 && mq <= 12480) {
+        rc = launch_qrcp_low(h, mq, n, Wq, mq, perm, (float*)bcast, st);
+        if (rc < 0) return rc;
+        if (rc == 0) {
+            k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
+            if ((rc = bqr_factor(h, mq, n, WqL, mq, tau, wy, st, -1))) return rc;
+            mixed_done = true;
+        }
+    }
+    h->last_qrcp = mixed_done ? MPJSVD_QRCP_MIXED : MPJSVD_QRCP_F64;
+    if (!mixed_done) {
+        if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1, bcast, qflags))) return rc;
+        k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
+    }
     k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, X, P.precond); ++h->launch_count;
     record(h, 1);
 
@@ -772,6 +787,49 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     return 0;
 }
 
+// The preconditioner's RRQR as a standalone call (mpjsvd_geqp3): A P = Q R with the QR of A P
+// in pivot order (geqrf layout) written over A and jpvt[j] = the column of A in position j.
+int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, double* tau)
+{
+    const size_t sz_tmp = align256(sizeof(double) * (size_t)m * n);
+    const size_t sz_bc = align256(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas));
+    const size_t sz_wy = align256(sizeof(double) * bqr_wbuf_doubles(n));
+    const size_t sz_fl = align256(sizeof(int) * (size_t)n);
+    int rc = ensure_buffer(&h->ws, &h->ws_bytes, sz_tmp + sz_bc + sz_wy + sz_fl);
+    if (rc) return rc;
+    char* base = (char*)h->ws;
+    double* tmp = (double*)base;
+    double* bcast = (double*)(base + sz_tmp);
+    double* wy = (double*)(base + sz_tmp + sz_bc);
+    int* flags = (int*)(base + sz_tmp + sz_bc + sz_wy);
+    DevState* st = (DevState*)h->dstate;
+    cudaStream_t s = h->stream;
+    const int egrid = h->num_sms * 4;
+    h->launch_count = 0;
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    if (e != cudaSuccess) return cuda_fail("memset state", e);
+    bool mixed_done = false;
+    if (h->params.qrcp == MPJSVD_QRCP_MIXED && bqr_nb(m) > 0 && m <= 12480) {
+        rc = launch_qrcp_low(h, m, n, A, lda, jpvt, (float*)bcast, st);
+        if (rc < 0) return rc;
+        if (rc == 0) {
+            k_gather_cols<<<std::min(n, egrid), 256, 0, s>>>(m, n, A, lda, jpvt, tmp, m, st); ++h->launch_count;
+            if ((rc = bqr_factor(h, m, n, tmp, m, tau, wy, st, -1))) return rc;
+            mixed_done = true;
+        }
+    }
+    h->last_qrcp = mixed_done ? MPJSVD_QRCP_MIXED : MPJSVD_QRCP_F64;
+    if (!mixed_done) {
+        if ((rc = launch_hhqr(h, true, m, n, A, lda, tau, jpvt, st, -1, bcast, flags))) return rc;
+        k_gather_cols<<<std::min(n, egrid), 256, 0, s>>>(m, n, A, lda, jpvt, tmp, m, st); ++h->launch_count;
+    }
+    e = cudaMemcpy2DAsync(A, sizeof(double) * lda, tmp, sizeof(double) * m, sizeof(double) * m, n,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail("geqp3 copy back", e);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : cuda_fail("geqp3 kernels", e);
+}
+
 int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
 {
     DevState st;
@@ -792,6 +850,7 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     r.block_w_low = st.branch == 0 ? h->last_block_w_low : 0;
     r.block_w_work = h->last_block_w_work;
     r.launches = h->launch_count;
+    r.qrcp = h->last_qrcp;
     if (h->params.timing && h->have_events) {
         float* t[6] = {&r.ms_qr, &r.ms_branch, &r.ms_low, &r.ms_switch, &r.ms_work, &r.ms_final};
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(t[i], h->ev[i], h->ev[i + 1]);

@@ -18,20 +18,22 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmpjsvd.so")
 
 MODE = {"auto": 0, "mixed": 1, "plain": 2}
 PRECOND = {"rt": 0, "r": 1}
+QRCP = {"mixed": 0, "f64": 1}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
 EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsvd_set_params",
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
            "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
-           "mpjsvd_apply_q"]
+           "mpjsvd_apply_q", "mpjsvd_geqp3"]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("tol_alg", ctypes.c_double), ("tol_orth", ctypes.c_double),
                 ("tol_cond_coef", ctypes.c_double), ("trailing_frac", ctypes.c_double),
                 ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
-                ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
+                ("qrcp", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -42,7 +44,7 @@ class Stats(ctypes.Structure):
                 ("block_w_work", ctypes.c_int), ("ms_qr", ctypes.c_float),
                 ("ms_branch", ctypes.c_float), ("ms_low", ctypes.c_float),
                 ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
-                ("ms_final", ctypes.c_float), ("launches", ctypes.c_int)]
+                ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -79,6 +81,7 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_svd_noalloc.argtypes = [_i, _i, _vp, _i, _vp, _vp, _vp, _d, _vp]
     L.mpjsvd_geqrf.argtypes = [_vp, _i, _i, _vp, _i, _vp]
     L.mpjsvd_apply_q.argtypes = [_vp, _i, _i, _i, _vp, _i, _vp, _vp, _i]
+    L.mpjsvd_geqp3.argtypes = [_vp, _i, _i, _vp, _i, _vp, _vp]
     _lib = L
     return L
 
@@ -99,6 +102,8 @@ def mpjsvd_default_params(**overrides):
             v = MODE[v]
         if k == "precond" and isinstance(v, str):
             v = PRECOND[v]
+        if k == "qrcp" and isinstance(v, str):
+            v = QRCP[v]
         setattr(p, k, v)
     return p
 
@@ -163,6 +168,10 @@ def mpjsvd_geqrf(h, m, n, A_ptr, lda, tau_ptr):
     return load_library().mpjsvd_geqrf(h, m, n, _vp(A_ptr), lda, _vp(tau_ptr))
 
 
+def mpjsvd_geqp3(h, m, n, A_ptr, lda, jpvt_ptr, tau_ptr):
+    return load_library().mpjsvd_geqp3(h, m, n, _vp(A_ptr), lda, _vp(jpvt_ptr), _vp(tau_ptr))
+
+
 def mpjsvd_apply_q(h, m, ncols, k, A_ptr, lda, tau_ptr, C_ptr, ldc):
     return load_library().mpjsvd_apply_q(h, m, ncols, k, _vp(A_ptr), lda, _vp(tau_ptr), _vp(C_ptr), ldc)
 
@@ -199,6 +208,8 @@ class Handle:
                 v = MODE[v]
             if k == "precond" and isinstance(v, str):
                 v = PRECOND[v]
+            if k == "qrcp" and isinstance(v, str):
+                v = QRCP[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 
@@ -256,6 +267,18 @@ class Handle:
         mpjsvd_set_stream(self.h, torch.cuda.current_stream(A.device).cuda_stream)
         _check(mpjsvd_geqrf(self.h, m, n, A.data_ptr(), A.stride(1), tau.data_ptr()), "mpjsvd_geqrf")
         return A, tau
+
+    def geqp3(self, A):
+        """The preconditioner's RRQR of a CUDA float64 (m, n) tensor (Alg. 5 unless params.qrcp
+        says binary64): returns (QR of A P in pivot order, jpvt, tau)."""
+        A = colmajor(A, A.device)  # a fresh column-major copy (factorized in place)
+        m, n = A.shape
+        jpvt = torch.empty(n, dtype=torch.int32, device=A.device)
+        tau = torch.empty(n, dtype=torch.float64, device=A.device)
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(A.device).cuda_stream)
+        _check(mpjsvd_geqp3(self.h, m, n, A.data_ptr(), A.stride(1), jpvt.data_ptr(), tau.data_ptr()),
+               "mpjsvd_geqp3")
+        return A, jpvt, tau
 
     def apply_q(self, QR, tau, C):
         """Q C for Q from geqrf (QR: (m, k) reflectors, tau: k); returns a new tensor."""

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     txt = open(os.path.join(ROOT, "include", "mpjsvd.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpjsvd_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(mpjsvd_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -41,14 +41,27 @@ def test_binding_names_match_header():
         assert callable(getattr(mpjsvd, name))
 
 
-def test_struct_sizes_match_header(lib_path):
-    """The ctypes mirrors of mpjsvd_params / mpjsvd_stats have the C layout."""
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of mpjsvd_params / mpjsvd_stats have the C layout: gcc compiles the
+    header and reports sizeof and offsetof of every field."""
+    import subprocess
     from paper_2209_04626_gb300 import mpjsvd
-    # 4 doubles + 6 ints
-    assert ctypes.sizeof(mpjsvd.Params) == 4 * 8 + 6 * 4
-    # 4 ints, 2 long long, 2 doubles, 2 ints, 6 floats, 1 int, padded to 8 bytes
-    raw = 4 * 4 + 2 * 8 + 2 * 8 + 2 * 4 + 6 * 4 + 4
-    assert ctypes.sizeof(mpjsvd.Stats) == (raw + 7) // 8 * 8
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpjsvd.h"', "int main(void) {"]
+    for cname, cls in (("mpjsvd_params", mpjsvd.Params), ("mpjsvd_stats", mpjsvd.Stats)):
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split("\n") if l)
+    for cname, cls in (("mpjsvd_params", mpjsvd.Params), ("mpjsvd_stats", mpjsvd.Stats)):
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(out["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
 
 
 def test_default_params_are_the_papers(lib_path):
