@@ -115,7 +115,8 @@ int mpjsvd_set_stream(mpjsvd_handle h, void* cuda_stream);
 int mpjsvd_set_params(mpjsvd_handle h, const mpjsvd_params* p);
 
 /* Thin SVD of one matrix (Algorithm 4).
- *   m, n : 1 <= n <= m <= 24576, n <= 12288
+ *   m, n : 1 <= n <= m <= 24576, n <= 8192 (a visit of the sweeps keeps its columns' n rows
+ *          in one CTA's registers)
  *   A    : device, m x n, leading dimension lda >= m; not modified. Entries must be finite
  *          (else MPJSVD_STATUS_NONFINITE) and their squares summed over a column must not
  *          overflow binary64 (|a_ij| well below 1e154; column norms are not pre-scaled)

@@ -137,7 +137,7 @@ int mpjsvd_svd(mpjsvd_handle h, int m, int n, const double* A, int lda, double* 
 {
     if (!h) return -1;
     if (m < 1 || m < n || m > 24576) return -2;
-    if (n < 1 || n > 12288) return -3;
+    if (n < 1 || n > 8192) return -3;
     if (!A) return -4;
     if (lda < m) return -5;
     if (!U) return -6;

@@ -54,6 +54,9 @@ int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st,
                       int gate_want, int* threads_out);
 int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
                       int phase, int gate_want, int* threads_out);
+// largest block width <= w_want whose register-resident visit holds mX rows (0: none)
+int sweep_fit_w_f32(int mX, int w_want);
+int sweep_fit_w_f64(int mX, int w_want);
 
 // blocked Householder QR and compact-WY application of Q (qr_blocked.cu)
 int bqr_nb(int m);                       // panel width for m rows; 0: use the unblocked kernels

@@ -74,6 +74,10 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads
     __shared__ double wv[NB];
     __shared__ double red[kPanelThreads / 32];
     __shared__ double refl[3];               // tau, beta, 1 / (alpha - beta) of this step
+    __shared__ double ex4[2][kPanelCl][4];   // per CTA: S, R(j,j+1), A(j+1,j+1), v(j+1) partials
+    __shared__ double part2[1];
+    __shared__ double nxt[2];                // next step's |tail|^2 and diagonal entry
+    __shared__ int s_fresh;
     if (gate_skip(st, gate_want)) return;  // uniform over the cluster
     cg::cluster_group cl = cg::this_cluster();
     const int cr = (int)cl.block_rank();
@@ -97,39 +101,65 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads
     // Every binary64 instruction occupies the FP64 unit of the warp's SM sub-partition, so
     // scalar work (the sums over warps and CTAs, the reflector) runs in warp 0 alone and is
     // broadcast through shared memory; 8-way sums are 3-level shuffle trees.
+    //
+    // One exchange per column: H_j preserves the norm of column j+1 over rows >= j, so with S
+    // = |A(j:, j+1)|^2 (summed in the same pass as the dot products), the new entries
+    // a = R(j, j+1) and alpha' = A'(j+1, j+1), the next reflector's |tail|^2 = S - a^2 - alpha'^2.
+    // It is used only when it keeps almost all of S ((S - a^2) >= S/2 and the tail >= half of
+    // that: then it is as accurate as a direct sum, and never mistakes rounding noise for a
+    // tail); otherwise, and at the panel's first column, the next step sums it exactly.
+    bool fresh = true;
     for (int j = 0; j < nbp; ++j) {
         const int par = j & 1;
         const int lj = j0 + j - base;  // local row of the diagonal entry (may lie outside)
         const int rlo = max(0, lj + 1);
         double* colj = psm + j * ldp;
-        // ---- |tail|^2 and the diagonal entry, summed over the cluster
-        double s = 0.0;
-        for (int r = rlo + tid; r < nr; r += kPanelThreads) s = fma(colj[r], colj[r], s);
-        s = warp_sum(s);
-        if (lane == 0) red[wid] = s;
-        __syncthreads();
-        MPJ_PANEL_PROBE(0)
-        if (wid == 0) {
-            double t = (lane < NW) ? red[lane] : 0.0;
-            t += __shfl_xor_sync(0xffffffffu, t, 4);
-            t += __shfl_xor_sync(0xffffffffu, t, 2);
-            t += __shfl_xor_sync(0xffffffffu, t, 1);
-            if (lane < kPanelCl) {
-                double* peer = cl.map_shared_rank(&exn[par][cr][0], lane);
-                peer[0] = t;
-                peer[1] = (lj >= 0 && lj < nr) ? colj[lj] : 0.0;
+        if (fresh) {
+            // ---- |tail|^2 and the diagonal entry, summed over the cluster
+            double s = 0.0;
+            for (int r = rlo + tid; r < nr; r += kPanelThreads) s = fma(colj[r], colj[r], s);
+            s = warp_sum(s);
+            if (lane == 0) red[wid] = s;
+            __syncthreads();
+            MPJ_PANEL_PROBE(0)
+            if (wid == 0) {
+                double t = (lane < NW) ? red[lane] : 0.0;
+                t += __shfl_xor_sync(0xffffffffu, t, 4);
+                t += __shfl_xor_sync(0xffffffffu, t, 2);
+                t += __shfl_xor_sync(0xffffffffu, t, 1);
+                if (lane < kPanelCl) {
+                    double* peer = cl.map_shared_rank(&exn[par][cr][0], lane);
+                    peer[0] = t;
+                    peer[1] = (lj >= 0 && lj < nr) ? colj[lj] : 0.0;
+                }
             }
+            MPJ_PANEL_PROBE(1)
+            cl.sync();
+            MPJ_PANEL_PROBE(2)
         }
-        MPJ_PANEL_PROBE(1)
-        cl.sync();
-        MPJ_PANEL_PROBE(2)
+        // ---- at the same time: warp 0 the reflector's scalars, warp 1 S = |A(j:, j+1)|^2,
+        // warps 2..NW-1 the dot products of the UNSCALED tail with the later columns (the
+        // reflector's scale 1/(alpha - beta) is applied to the partial sums afterwards)
+        const int na = nbp - j - 1;
+        int cpw = 1;
+        while (cpw < na) cpw <<= 1;
+        const int sub = 32 / cpw;
+        const int ci = lane & (cpw - 1), sg = lane / cpw;
+        const bool colok = ci < na;
+        double* colc = psm + (j + 1 + (colok ? ci : 0)) * ldp;
         if (wid == 0) {
-            double sq = (lane < kPanelCl) ? exn[par][lane][0] : 0.0;
-            double al = (lane < kPanelCl) ? exn[par][lane][1] : 0.0;  // one nonzero
+            double sq, al;
+            if (fresh) {
+                sq = (lane < kPanelCl) ? exn[par][lane][0] : 0.0;
+                al = (lane < kPanelCl) ? exn[par][lane][1] : 0.0;  // one nonzero
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                al += __shfl_xor_sync(0xffffffffu, al, o);
+                for (int o = 4; o > 0; o >>= 1) {
+                    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                }
+            } else {
+                sq = nxt[0];
+                al = nxt[1];
             }
             if (lane == 0) {
                 // with y = 1/|x|: beta = -sign(alpha)|x|, tau = (beta - alpha)/beta = 1 +
@@ -155,36 +185,56 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads
                 refl[2] = rden;
                 if (cr == 0) tau[j0 + j] = tj;
             }
+        } else if (wid == 1) {
+            if (na > 0) {
+                const double* c1 = psm + (j + 1) * ldp;
+                double sacc = 0.0;
+                for (int r = max(0, lj) + lane; r < nr; r += 32) sacc = fma(c1[r], c1[r], sacc);
+                sacc = warp_sum(sacc);
+                if (lane == 0) part2[0] = sacc;
+            }
+        } else {
+            // every lane of the warp reaches the full-mask shuffles (acc = 0 on idle lanes)
+            double acc = 0.0;
+            if (colok)
+                for (int r = rlo + (wid - 2) * sub + sg; r < nr; r += (NW - 2) * sub) acc = fma(colj[r], colc[r], acc);
+            for (int o = cpw; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (sg == 0 && colok) part[wid - 2][ci] = acc;
         }
         __syncthreads();
         MPJ_PANEL_PROBE(3)
         const double tj = refl[0], rden = refl[2];
-        for (int r = rlo + tid; r < nr; r += kPanelThreads) colj[r] *= rden;
-        if (tid == 0 && lj >= 0 && lj < nr) colj[lj] = refl[1];
-        __syncthreads();
-        const int na = nbp - j - 1;
-        if (na == 0 || tj == 0.0) continue;  // tj is identical in every CTA of the cluster
-        // ---- w_c = v^T A(:, c) for the na later panel columns. Lane split: cpw lanes per
-        // row (one per column), sub = 32 / cpw rows per warp at a time.
-        int cpw = 1;
-        while (cpw < na) cpw <<= 1;
-        const int sub = 32 / cpw;
-        const int ci = lane & (cpw - 1), sg = lane / cpw;
-        const int rs = max(0, lj) + wid * sub + sg, rstep = NW * sub;
-        const bool colok = ci < na;
-        double* colc = psm + (j + 1 + (colok ? ci : 0)) * ldp;
-        double acc = 0.0;
-        if (colok)
-            for (int r = rs; r < nr; r += rstep) acc = fma(r == lj ? 1.0 : colj[r], colc[r], acc);
-        for (int o = cpw; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (sg == 0 && colok) part[wid][ci] = acc;
-        __syncthreads();
+        if (na == 0 || tj == 0.0) {  // tj is identical in every CTA of the cluster
+            for (int r = rlo + tid; r < nr; r += kPanelThreads) colj[r] *= rden;
+            if (tid == 0 && lj >= 0 && lj < nr) colj[lj] = refl[1];
+            __syncthreads();
+            fresh = true;
+            continue;
+        }
         MPJ_PANEL_PROBE(4)
         if (tid < na) {
-            const double p = ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) +
-                             ((part[4][tid] + part[5][tid]) + (part[6][tid] + part[7][tid]));
+            // this CTA's share of v^T A(:, c): rden * (unscaled dots) + the diagonal row's entry
+            const double d = ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) +
+                             (part[4][tid] + part[5][tid]);
+            const double a = (lj >= 0 && lj < nr) ? psm[(j + 1 + tid) * ldp + lj] : 0.0;
+            const double p = fma(rden, d, a);
 #pragma unroll
             for (int q = 0; q < kPanelCl; ++q) *cl.map_shared_rank(&exd[par][cr][tid], q) = p;
+        } else if (tid == 32) {
+            // S, R(j, j+1) before the update, A(j+1, j+1) and v(j+1): the owners contribute
+            const double sp = part2[0];
+            const int l1 = lj + 1;
+            const double aj = (lj >= 0 && lj < nr) ? psm[(j + 1) * ldp + lj] : 0.0;
+            const double aj1 = (l1 >= 0 && l1 < nr) ? psm[(j + 1) * ldp + l1] : 0.0;
+            const double vj1 = (l1 >= 0 && l1 < nr) ? colj[l1] * rden : 0.0;
+#pragma unroll
+            for (int q = 0; q < kPanelCl; ++q) {
+                double* peer = cl.map_shared_rank(&ex4[par][cr][0], q);
+                peer[0] = sp;
+                peer[1] = aj;
+                peer[2] = aj1;
+                peer[3] = vj1;
+            }
         }
         MPJ_PANEL_PROBE(5)
         cl.sync();
@@ -194,13 +244,46 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads
             const double w = ((e[0][tid] + e[1][tid]) + (e[2][tid] + e[3][tid])) +
                              ((e[4][tid] + e[5][tid]) + (e[6][tid] + e[7][tid]));
             wv[tid] = tj * w;
+        } else if (wid == 1) {
+            // the next column's reflector inputs, downdated, in one warp: lane l holds quantity
+            // l / 8 (S, R(j,j+1), A(j+1,j+1), v(j+1)) of CTA l % 8, and w_{j+1}; 3-level trees
+            // over CTAs in the association order of the sums above (bit-identical results)
+            const int q = lane & 7, kq = lane >> 3;
+            double v = ex4[par][q][kq];
+            double w = exd[par][q][0];
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            const double S = __shfl_sync(0xffffffffu, v, 0);
+            const double aj = __shfl_sync(0xffffffffu, v, 8);
+            const double aj1 = __shfl_sync(0xffffffffu, v, 16);
+            const double vj1 = __shfl_sync(0xffffffffu, v, 24);
+            if (lane == 0) {
+                const double wj = tj * w;
+                const double a1 = fma(-wj, 1.0, aj);
+                const double alpha1 = fma(-wj, vj1, aj1);
+                const double T = fma(-a1, a1, S);
+                const double tail = fma(-alpha1, alpha1, T);
+                const bool ok = (T >= 0.5 * S) && (tail >= 0.5 * T);
+                nxt[0] = tail;
+                nxt[1] = alpha1;
+                s_fresh = ok ? 0 : 1;
+            }
         }
+        // column j becomes the reflector: scaled tail, beta on the diagonal (the same product
+        // x * rden as v(j+1) above, so the downdated alpha' equals the stored update)
+        for (int r = rlo + tid; r < nr; r += kPanelThreads) colj[r] *= rden;
         __syncthreads();
+        if (tid == 0 && lj >= 0 && lj < nr) colj[lj] = refl[1];
         MPJ_PANEL_PROBE(7)
-        // ---- A(:, c) -= tau w_c v
+        fresh = s_fresh != 0;
+        // ---- A(:, c) -= tau w_c v (all NW warps: each row exactly once; v(lj) = 1)
         if (colok) {
             const double wc = wv[ci];
-            for (int r = rs; r < nr; r += rstep) colc[r] = fma(-wc, r == lj ? 1.0 : colj[r], colc[r]);
+            const int rs8 = max(0, lj) + wid * sub + sg, rstep8 = NW * sub;
+            for (int r = rs8; r < nr; r += rstep8) colc[r] = fma(-wc, r == lj ? 1.0 : colj[r], colc[r]);
         }
         __syncthreads();
         MPJ_PANEL_PROBE(8)

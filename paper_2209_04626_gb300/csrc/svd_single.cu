@@ -712,8 +712,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
 
     // ---- [3.2] binary32 Jacobi on low(X), U only (gated)
     const size_t nn = (size_t)n * n;
-    int w_low = pick_w(n, n, true, h->num_sms, P.block_w);
-    int w_work = pick_w(n, n, false, h->num_sms, P.block_w);
+    // the register file bounds the width for tall X: fall back to narrower blocks
+    int w_low = sweep_fit_w_f32(n, pick_w(n, n, true, h->num_sms, P.block_w));
+    int w_work = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
+    if (w_low == 0 || w_work == 0)
+        return cuda_fail("sweeps: no register-resident variant holds n rows", cudaErrorInvalidValue);
     h->last_block_w_low = (P.mode == MPJSVD_MODE_PLAIN) ? 0 : w_low;
     h->last_block_w_work = w_work;
     if (P.mode != MPJSVD_MODE_PLAIN) {

@@ -551,8 +551,9 @@ __device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj,
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
+        // tight acquire spin (the wait is usually a few microseconds), time-bounded
         while (ld_acquire_u32(ver + bi) < R || ld_acquire_u32(ver + bj) < R) {
-            if ((++spins & 63u) == 0) {
+            if ((++spins & 255u) == 0) {
                 if (call_failed(st)) {
                     ok = 0;
                     break;
@@ -563,7 +564,6 @@ __device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj,
                     break;
                 }
             }
-            __nanosleep(32);
         }
         s_ok = ok;
     }

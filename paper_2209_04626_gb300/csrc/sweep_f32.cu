@@ -10,12 +10,42 @@ static int try_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st, in
 #define MPJ_L(WW, RR) \
     if (w == WW && rpt == RR) return launch_sweeps_wr<float, false, WW, RR>(h, D, X, nullptr, st, phase, gate_want, threads)
     MPJ_L(1, 2); MPJ_L(1, 4); MPJ_L(1, 8); MPJ_L(1, 16);
-    MPJ_L(2, 2); MPJ_L(2, 4); MPJ_L(2, 8);
+    MPJ_L(2, 2); MPJ_L(2, 4); MPJ_L(2, 8); MPJ_L(2, 16);
     MPJ_L(4, 2); MPJ_L(4, 4); MPJ_L(4, 8);
     MPJ_L(8, 2); MPJ_L(8, 4); MPJ_L(8, 8);
     MPJ_L(16, 2); MPJ_L(16, 4);
 #undef MPJ_L
     return -1;
+}
+
+// Register-limited thread count of variant (w, rpt), 0 if it is not instantiated.
+static int max_threads_f32(int w, int rpt)
+{
+    cudaFuncAttributes fa;
+#define MPJ_Q(WW, RR) \
+    if (w == WW && rpt == RR) return cudaFuncGetAttributes(&fa, k_sweeps<float, false, WW, RR>) == cudaSuccess ? fa.maxThreadsPerBlock : 0
+    MPJ_Q(1, 2); MPJ_Q(1, 4); MPJ_Q(1, 8); MPJ_Q(1, 16);
+    MPJ_Q(2, 2); MPJ_Q(2, 4); MPJ_Q(2, 8); MPJ_Q(2, 16);
+    MPJ_Q(4, 2); MPJ_Q(4, 4); MPJ_Q(4, 8);
+    MPJ_Q(8, 2); MPJ_Q(8, 4); MPJ_Q(8, 8);
+    MPJ_Q(16, 2); MPJ_Q(16, 4);
+#undef MPJ_Q
+    return 0;
+}
+
+// Largest block width <= w_want (a power of two) with a variant whose register-resident
+// visit holds mX rows: some rpt with w * rpt <= 64 and ceil(mX / rpt) threads allowed by the
+// variant's register use. 0: none.
+int sweep_fit_w_f32(int mX, int w_want)
+{
+    for (int w = w_want; w >= 1; w /= 2)
+        for (int rpt = 2; rpt <= 16 && w * rpt <= 64; rpt *= 2) {
+            const int need = (mX + rpt - 1) / rpt;
+            if (need > 1024) continue;
+            const int mt = max_threads_f32(w, rpt);
+            if (mt > 0 && sweep_threads(mX, rpt) <= mt) return w;
+        }
+    return 0;
 }
 
 // Block width w in {1, 2, 4, 8, 16}; w * rpt <= 64 floats per thread.

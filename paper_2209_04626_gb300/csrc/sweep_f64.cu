@@ -17,6 +17,34 @@ static int try_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevS
     return -1;
 }
 
+// Register-limited thread count of variant (w, rpt), 0 if it is not instantiated.
+static int max_threads_f64(int w, int rpt)
+{
+    cudaFuncAttributes fa;
+#define MPJ_Q(WW, RR) \
+    if (w == WW && rpt == RR) return cudaFuncGetAttributes(&fa, k_sweeps<double, true, WW, RR>) == cudaSuccess ? fa.maxThreadsPerBlock : 0
+    MPJ_Q(1, 2); MPJ_Q(1, 4); MPJ_Q(1, 8); MPJ_Q(1, 16);
+    MPJ_Q(2, 2); MPJ_Q(2, 4); MPJ_Q(2, 8); MPJ_Q(2, 16);
+    MPJ_Q(4, 2); MPJ_Q(4, 4); MPJ_Q(4, 8);
+    MPJ_Q(8, 2); MPJ_Q(8, 4);
+#undef MPJ_Q
+    return 0;
+}
+
+// Largest block width <= w_want (a power of two) with a variant whose register-resident
+// visit holds mX rows (w * rpt <= 32 doubles per thread). 0: none.
+int sweep_fit_w_f64(int mX, int w_want)
+{
+    for (int w = w_want; w >= 1; w /= 2)
+        for (int rpt = 2; rpt <= 16 && w * rpt <= 32; rpt *= 2) {
+            const int need = (mX + rpt - 1) / rpt;
+            if (need > 1024) continue;
+            const int mt = max_threads_f64(w, rpt);
+            if (mt > 0 && sweep_threads(mX, rpt) <= mt) return w;
+        }
+    return 0;
+}
+
 // Block width w in {1, 2, 4, 8}; rows per thread chosen so that the visit's 2w columns fit
 // in registers (w * rpt <= 32 doubles per thread), doubled while a variant's register use
 // does not allow the thread count.
