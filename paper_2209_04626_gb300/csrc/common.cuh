@@ -41,7 +41,6 @@ struct DevState {
     double maxnorm;        // max column norm of X (branch test)
     unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
-    unsigned wy_count[2];                  // blocked QR: Gram tiles finished, per stream
     unsigned long long amax_bits;          // Alg. 5: max |a_ij| (bits of a non-negative double)
     float4 cand_sc[512];                   // Alg. 5: candidate's (alpha, |tail|, |col|) x parity
 };

@@ -60,7 +60,7 @@ int sweep_fit_w_f64(int mX, int w_want);
 
 // blocked Householder QR and compact-WY application of Q (qr_blocked.cu)
 int bqr_nb(int m);                       // panel width for m rows; 0: use the unblocked kernels
-size_t bqr_wbuf_doubles(int ncols_max);  // scratch for bqr_factor / bqr_apply
+size_t bqr_wbuf_doubles(int ncols_max, int m_max);  // scratch for bqr_factor / bqr_apply
 int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
                int gate_want);
 int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,

@@ -61,11 +61,9 @@ __device__ __forceinline__ double refl_at(const double* V, int ldv, int j0, int 
 // ------------------------------------------------------------------------------------------
 // Panel factorization: columns j0 .. j0+nbp-1, rows j0 .. m-1 of A, nbp <= NB. CTA q of the
 // cluster holds rows j0 + q*rpc .. j0 + (q+1)*rpc - 1 in shared memory (column-major, odd ld).
-// Also zeroes wz[0 .. nwz) and wz2[0 .. nwz2) for the following k_wy_w launches.
 template <int NB>
 __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads)
-    k_panel_qr(int m, int j0, int nbp, double* A, int lda, double* tau, double* wz, int nwz,
-               double* wz2, int nwz2, DevState* st, int gate_want)
+    k_panel_qr(int m, int j0, int nbp, double* A, int lda, double* tau, DevState* st, int gate_want)
 {
     extern __shared__ double psm[];
     __shared__ double exn[2][kPanelCl][2];   // per CTA: partial |tail|^2, diagonal entry
@@ -90,8 +88,6 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(kPanelThreads
     const int base = j0 + cr * rpc;
     const int nr = max(0, min(rpc, m - base));
 
-    for (int i = cr * kPanelThreads + tid; i < nwz; i += kPanelCl * kPanelThreads) wz[i] = 0.0;
-    for (int i = cr * kPanelThreads + tid; i < nwz2; i += kPanelCl * kPanelThreads) wz2[i] = 0.0;
     for (int c = 0; c < NB; ++c)
         for (int r = tid; r < rpc; r += kPanelThreads)
             psm[c * ldp + r] = (c < nbp && r < nr) ? A[cm(base + r, j0 + c, lda)] : 0.0;
@@ -330,28 +326,34 @@ __device__ void build_T(const double* G, const double* tau, int j0, int nbp, dou
     }
 }
 
-// W(k, c) += sum_r v_k(r) C(r, c0 + c) over one tile of kWyRc rows (from j0 + blockIdx.y *
-// kWyRc) and 32 columns (strip blockIdx.x); the strip after the last one forms the Gram
-// matrix V^T V into W(:, ncols .. ncols + NB). W is NB x (ncols + NB), ld NB, zeroed. The last
-// CTA of the Gram strip to finish (counted in *count, which it resets) builds T into Tout.
+// One accumulator set of the compact-WY update: the final W (NB x (ncols + NB), ld NB: V^T C
+// then the Gram matrix V^T V), T (NB x NB), one partial W per row chunk and column strip, and
+// a counter per strip (zero between uses).
+struct WySet {
+    double* W;
+    double* T;
+    double* Wp;
+    unsigned* cnt;
+};
+constexpr int kWyMaxChunks = 32;
+
+// Partial W(k, c) = sum_r v_k(r) C(r, c0 + c) over row chunk blockIdx.y (spc tiles of kWyRc
+// rows) and the 32 columns of strip blockIdx.x; the strip after the last one forms the Gram
+// matrix V^T V. Each CTA stores its partial; the last CTA of a strip to finish (per-strip
+// counter) sums the partials in chunk order (the result does not depend on timing), and for
+// the Gram strip builds T.
 template <int NB>
 __global__ void __launch_bounds__(kWyThreads)
     k_wy_w(int m, int j0, int nbp, const double* V, int ldv, const double* C, int ldc, int c0,
-           int ncols, double* W, const double* tau, double* Tout, unsigned* count, DevState* st,
-           int gate_want)
+           int ncols, int spc, WySet ws, const double* tau, DevState* st, int gate_want)
 {
     __shared__ double Vs[NB][kWyRc + 1];
     __shared__ int s_last;
     if (gate_skip(st, gate_want)) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nstrips = (ncols + 31) / 32;
-    const bool is_gram = (int)blockIdx.x == nstrips;
-    const int r0 = j0 + blockIdx.y * kWyRc;
-    for (int e = tid; e < NB * kWyRc; e += kWyThreads) {
-        const int k = e / kWyRc, r = e % kWyRc, gr = r0 + r;
-        Vs[k][r] = (k < nbp && gr < m) ? refl_at(V, ldv, j0, k, gr) : 0.0;
-    }
-    __syncthreads();
+    const int strip = blockIdx.x;
+    const bool is_gram = strip == nstrips;
     constexpr int CG = 32 / NB;                       // column groups per warp
     constexpr int CPT = 32 / (kWyThreads / 32 * CG);  // columns per thread
     const int k = lane % NB;
@@ -362,47 +364,60 @@ __global__ void __launch_bounds__(kWyThreads)
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
         const int c = cl0 + i;
-        ok[i] = is_gram ? (c < nbp) : (blockIdx.x * 32 + c < ncols);
-        cp[i] = (ok[i] && !is_gram) ? C + (size_t)(c0 + blockIdx.x * 32 + c) * ldc : C;
+        ok[i] = is_gram ? (c < nbp) : (strip * 32 + c < ncols);
+        cp[i] = (ok[i] && !is_gram) ? C + (size_t)(c0 + strip * 32 + c) * ldc : C;
     }
     double acc[CPT];
 #pragma unroll
     for (int i = 0; i < CPT; ++i) acc[i] = 0.0;
-    const int rend = min(kWyRc, m - r0);
-    for (int r = 0; r < rend; ++r) {
-        const double v = Vs[k][r];
-        const int gr = r0 + r;
+    for (int sc = 0; sc < spc; ++sc) {
+        const int r0 = j0 + (blockIdx.y * spc + sc) * kWyRc;
+        if (r0 >= m) break;
+        __syncthreads();  // Vs of the previous tile is no longer read
+        for (int e = tid; e < NB * kWyRc; e += kWyThreads) {
+            const int kk = e / kWyRc, r = e % kWyRc, gr = r0 + r;
+            Vs[kk][r] = (kk < nbp && gr < m) ? refl_at(V, ldv, j0, kk, gr) : 0.0;
+        }
+        __syncthreads();
+        const int rend = min(kWyRc, m - r0);
+        for (int r = 0; r < rend; ++r) {
+            const double v = Vs[k][r];
+            const int gr = r0 + r;
 #pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            double c;
-            if (is_gram) c = ok[i] ? Vs[cl0 + i][r] : 0.0;
-            else c = ok[i] ? cp[i][gr] : 0.0;
-            acc[i] = fma(v, c, acc[i]);
+            for (int i = 0; i < CPT; ++i) {
+                double c;
+                if (is_gram) c = ok[i] ? Vs[cl0 + i][r] : 0.0;
+                else c = ok[i] ? cp[i][gr] : 0.0;
+                acc[i] = fma(v, c, acc[i]);
+            }
         }
     }
-    if (k < nbp) {
+    double* mine = ws.Wp + ((size_t)blockIdx.y * (nstrips + 1) + strip) * (NB * 32);
 #pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            if (!ok[i]) continue;
-            const int c = is_gram ? ncols + cl0 + i : blockIdx.x * 32 + cl0 + i;
-            atomicAdd(&W[(size_t)c * NB + k], acc[i]);
-        }
-    }
-    if (!is_gram) return;
-    // last Gram CTA: every partial Gram is in W once the counter reaches gridDim.y
+    for (int i = 0; i < CPT; ++i) mine[(cl0 + i) * NB + k] = acc[i];
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(count, 1u) == gridDim.y - 1);
+    if (tid == 0) s_last = (atomicAdd(&ws.cnt[strip], 1u) == gridDim.y - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    const int ncs = is_gram ? NB : min(32, ncols - strip * 32);
+    for (int e = tid; e < NB * ncs; e += kWyThreads) {
+        const int kk = e % NB, c = e / NB;
+        double sum = 0.0;
+        for (int q = 0; q < (int)gridDim.y; ++q)
+            sum += __ldcg(ws.Wp + ((size_t)q * (nstrips + 1) + strip) * (NB * 32) + c * NB + kk);
+        ws.W[(size_t)(is_gram ? ncols + c : strip * 32 + c) * NB + kk] = sum;
+    }
+    if (tid == 0) ws.cnt[strip] = 0u;
+    if (!is_gram) return;
+    __syncthreads();
     static_assert(3 * NB * (NB + 1) <= NB * (kWyRc + 1), "T scratch must fit in the V tile");
     double(*Ts)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(&Vs[0][0]);
     double(*Gs)[NB + 1] = Ts + NB;
     double(*Ms)[NB + 1] = Ts + 2 * NB;
-    build_T<NB>(W + (size_t)ncols * NB, tau, j0, nbp, Ts, Gs, Ms);
-    for (int e = tid; e < NB * NB; e += kWyThreads) Tout[e] = Ts[e % NB][e / NB];
-    if (tid == 0) *count = 0u;
+    build_T<NB>(ws.W + (size_t)ncols * NB, tau, j0, nbp, Ts, Gs, Ms);
+    for (int e = tid; e < NB * NB; e += kWyThreads) ws.T[e] = Ts[e % NB][e / NB];
 }
 
 // C(r, c0 + c) -= sum_k v_k(r) W'(k, c), W' = op(T) W(:, strip), over a tile of kWyRc rows x
@@ -504,29 +519,50 @@ int bqr_nb(int m)
     return 0;
 }
 
-// narrow accumulator + T, then two wide accumulators + T (see bqr_factor_nb)
-size_t bqr_wbuf_doubles(int ncols_max)
+// Row chunks of a step with m - j0 <= m_max rows (at most kWyMaxChunks).
+static int wy_chunks_max(int m_max) { return std::max(1, std::min(kWyMaxChunks, (m_max + kWyRc - 1) / kWyRc)); }
+
+// Doubles of one accumulator set for up to ncap columns and m_max rows (sized for NB = 32).
+static size_t wyset_doubles(int ncap, int m_max)
 {
-    return (size_t)32 * 64 + 32 * 32 + 2 * ((size_t)32 * ((size_t)ncols_max + 32) + 32 * 32);
+    const size_t ns = (size_t)(ncap + 31) / 32 + 1;
+    return (size_t)32 * ((size_t)ncap + 32) + 32 * 32 + (size_t)wy_chunks_max(m_max) * ns * 32 * 32 + (ns + 1) / 2 + 2;
+}
+static WySet wyset_at(double* base, int ncap, int m_max)
+{
+    const size_t ns = (size_t)(ncap + 31) / 32 + 1;
+    WySet w;
+    w.W = base;
+    w.T = w.W + (size_t)32 * ((size_t)ncap + 32);
+    w.Wp = w.T + 32 * 32;
+    w.cnt = (unsigned*)(w.Wp + (size_t)wy_chunks_max(m_max) * ns * 32 * 32);
+    return w;
+}
+static size_t wyset_cnt_bytes(int ncap) { return sizeof(unsigned) * ((size_t)(ncap + 31) / 32 + 1); }
+
+// a narrow set (the next panel's columns) and a wide set (the rest / a whole apply)
+size_t bqr_wbuf_doubles(int ncols_max, int m_max)
+{
+    return wyset_doubles(32, m_max) + wyset_doubles(ncols_max, m_max);
 }
 
 // One panel's compact-WY update C(j0:m, c0:c0+ncols) <- (I - V op(T) V^T) C with T built
 // from the panel's Gram matrix: op(T) = T^T applies Q_panel^T (QR trailing update), T applies
-// Q_panel (forming Q C). W: zeroed NB x (ncols + NB) accumulator followed by NB x NB for T;
-// count: a zeroed counter (left zeroed).
+// Q_panel (forming Q C). Rows are split into at most kWyMaxChunks chunks.
 template <int NB>
 static void wy_step(mpjsvd_ctx* h, cudaStream_t s, int m, int j0, int nbp, const double* V, int ldv,
-                    const double* tau, double* C, int ldc, int c0, int ncols, double* W, unsigned* count,
-                    bool trans, DevState* st, int gate_want)
+                    const double* tau, double* C, int ldc, int c0, int ncols, const WySet& ws, bool trans,
+                    DevState* st, int gate_want)
 {
     const int nstrips = (ncols + 31) / 32;
-    const int nchunks = (m - j0 + kWyRc - 1) / kWyRc;
-    double* T = W + (size_t)NB * (ncols + NB);
-    k_wy_w<NB><<<dim3(nstrips + 1, nchunks), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0, ncols, W,
-                                                                 tau, T, count, st, gate_want);
-    k_wy_update<NB><<<dim3(std::max(1, nstrips), nchunks), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0,
-                                                                               ncols, W, T, trans, st,
-                                                                               gate_want);
+    const int nsub = (m - j0 + kWyRc - 1) / kWyRc;
+    const int spc = (nsub + kWyMaxChunks - 1) / kWyMaxChunks;
+    const int nchunks = (nsub + spc - 1) / spc;
+    k_wy_w<NB><<<dim3(nstrips + 1, nchunks), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0, ncols, spc, ws,
+                                                                 tau, st, gate_want);
+    k_wy_update<NB><<<dim3(std::max(1, nstrips), nsub), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0,
+                                                                            ncols, ws.W, ws.T, trans, st,
+                                                                            gate_want);
     h->launch_count += 2;
 }
 
@@ -535,9 +571,8 @@ static void wy_step(mpjsvd_ctx* h, cudaStream_t s, int m, int j0, int nbp, const
 // on the side stream) overlaps the factorization of the next panel. Column ranges:
 // panel p = [j0, j0 + nbp), next panel = [cn0, cn0 + nbn), wide = [cw0, n). Panel p's
 // columns have received every earlier update once wide(p-2) (side) and narrow(p-1) (main,
-// in order) are done; the narrow update of p needs wide(p-1). W layout: narrow accumulator,
-// then two wide accumulators used by alternate panels (wide(p-1) may still read its own
-// while panel p zeroes the other), each followed by its NB x NB T.
+// in order) are done; the narrow update of p needs wide(p-1). The narrow and wide updates
+// use separate accumulator sets; successive wide updates run in order on the side stream.
 template <int NB>
 static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W,
                          DevState* st, int gate_want)
@@ -546,11 +581,11 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
     const size_t smax = sizeof(double) * NB * (size_t)(((m + kPanelCl - 1) / kPanelCl) | 1);
     cudaError_t e = cudaFuncSetAttribute(k_panel_qr<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (e != cudaSuccess) return cuda_fail("panel smem attribute", e);
+    const WySet wn = wyset_at(W, 32, m), ww = wyset_at(W + wyset_doubles(32, m), n, m);
+    if ((e = cudaMemsetAsync(wn.cnt, 0, wyset_cnt_bytes(32), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ww.cnt, 0, wyset_cnt_bytes(n), s)) != cudaSuccess)
+        return cuda_fail("wy counters", e);
     const bool la = h->have_side;
-    const size_t wsz = (size_t)NB * ((size_t)n + NB) + (size_t)NB * NB;
-    double* Wn = W;
-    double* Ww[2] = {W + (size_t)NB * 2 * NB + (size_t)NB * NB, nullptr};
-    Ww[1] = Ww[0] + wsz;
     int p = 0;
     for (int j0 = 0; j0 < n; j0 += NB, ++p) {
         const int nbp = std::min(NB, n - j0);
@@ -559,29 +594,20 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
         const size_t psmem = sizeof(double) * NB * (size_t)(((m - j0 + kPanelCl - 1) / kPanelCl) | 1);
         if (!la) {  // one stream: the whole trailing matrix at once
             const int nt = n - cn0;
-            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, Ww[0],
-                                                                 nt > 0 ? NB * (nt + NB) : 0, nullptr, 0,
-                                                                 st, gate_want);
+            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, st, gate_want);
             ++h->launch_count;
-            if (nt > 0)
-                wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nt, Ww[0], &st->wy_count[0], true,
-                            st, gate_want);
+            if (nt > 0) wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nt, ww, true, st, gate_want);
         } else {
             if (p >= 2 && (e = cudaStreamWaitEvent(s, h->qev[1 + (p - 2) % 3], 0)) != cudaSuccess) break;
-            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, Wn,
-                                                                 nbn > 0 ? NB * (nbn + NB) : 0, Ww[p & 1],
-                                                                 ncw > 0 ? NB * (ncw + NB) : 0, st, gate_want);
+            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, st, gate_want);
             ++h->launch_count;
             if ((e = cudaEventRecord(h->qev[0], s)) != cudaSuccess) break;
             if ((e = cudaStreamWaitEvent(h->side, h->qev[0], 0)) != cudaSuccess) break;
-            if (ncw > 0)
-                wy_step<NB>(h, h->side, m, j0, nbp, A, lda, tau, A, lda, cw0, ncw, Ww[p & 1],
-                            &st->wy_count[1], true, st, gate_want);
+            if (ncw > 0) wy_step<NB>(h, h->side, m, j0, nbp, A, lda, tau, A, lda, cw0, ncw, ww, true, st, gate_want);
             if ((e = cudaEventRecord(h->qev[1 + p % 3], h->side)) != cudaSuccess) break;
             if (nbn > 0) {
                 if (p >= 1 && (e = cudaStreamWaitEvent(s, h->qev[1 + (p - 1) % 3], 0)) != cudaSuccess) break;
-                wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nbn, Wn, &st->wy_count[0], true, st,
-                            gate_want);
+                wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nbn, wn, true, st, gate_want);
             }
         }
         e = cudaGetLastError();
@@ -597,7 +623,7 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
 }
 
 // Householder QR of the m x n (m >= n) column-major A in place (geqrf layout) with tau[n].
-// W: bqr_wbuf_doubles(n) doubles of scratch. Requires bqr_nb(m) > 0.
+// W: bqr_wbuf_doubles(n, m) doubles of scratch. Requires bqr_nb(m) > 0.
 int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
                int gate_want)
 {
@@ -610,20 +636,20 @@ int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, dou
 // C (m x ncols, leading rows of a matrix with ld ldc) <- Q C, Q = H_0 ... H_{k-1} from the k
 // reflectors stored in V (m x k, geqrf layout). ident: C holds the identity's first ncols
 // columns on entry, so panel p only touches columns >= its first (the structure of forming Q).
-// W: bqr_wbuf_doubles(ncols) doubles of scratch.
+// W: bqr_wbuf_doubles(ncols, m) doubles of scratch.
 int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,
               double* C, int ldc, bool ident, double* W, DevState* st, int gate_want)
 {
     constexpr int NB = 32;
+    const WySet ws = wyset_at(W + wyset_doubles(32, m), ncols, m);
+    cudaError_t e = cudaMemsetAsync(ws.cnt, 0, wyset_cnt_bytes(ncols), h->stream);
+    if (e != cudaSuccess) return cuda_fail("wy counters", e);
     for (int j0 = ((k - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
         const int nbp = std::min(NB, k - j0);
         const int cstart = ident ? j0 : 0;
         const int nc = ncols - cstart;
         if (nc <= 0) continue;
-        cudaError_t e = cudaMemsetAsync(W, 0, sizeof(double) * NB * (size_t)(nc + NB), h->stream);
-        if (e != cudaSuccess) return cuda_fail("wy memset", e);
-        wy_step<NB>(h, h->stream, m, j0, nbp, V, ldv, tau, C, ldc, cstart, nc, W, &st->wy_count[0], false, st,
-                    gate_want);
+        wy_step<NB>(h, h->stream, m, j0, nbp, V, ldv, tau, C, ldc, cstart, nc, ws, false, st, gate_want);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail("blocked apply kernels", e);
     }
@@ -632,7 +658,7 @@ int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, 
 
 int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau)
 {
-    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(n);
+    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(n, m);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;
@@ -645,7 +671,7 @@ int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau)
 int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int lda, const double* tau,
                  double* C, int ldc)
 {
-    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(ncols);
+    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(ncols, m);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;

@@ -467,7 +467,7 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_BCAST] = sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas);
     sz[L_FLAGS] = sizeof(int) * n;
     sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
-    sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n);
+    sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n, m);
     // The QRCP's broadcast slots are live only during the QR preconditioning; the buffers
     // from X up to V_acc are first written after it, so the slots share their memory when
     // they fit (L_BITS, zeroed at the start of a call, is not in that span).
@@ -796,7 +796,7 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
 {
     const size_t sz_tmp = align256(sizeof(double) * (size_t)m * n);
     const size_t sz_bc = align256(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas));
-    const size_t sz_wy = align256(sizeof(double) * bqr_wbuf_doubles(n));
+    const size_t sz_wy = align256(sizeof(double) * bqr_wbuf_doubles(n, m));
     const size_t sz_fl = align256(sizeof(int) * (size_t)n);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, sz_tmp + sz_bc + sz_wy + sz_fl);
     if (rc) return rc;
