@@ -181,6 +181,13 @@ __global__ void k_gemm(GemmArgs g, const int* gate, int gate_want)
     }
 }
 
+// Binary64 switch GEMMs (dgemm_tile); gate as k_gemm.
+__global__ void __launch_bounds__(kDgThreads) k_dgemm(GemmArgs g, const int* gate, int gate_want)
+{
+    if (gate && *(volatile const int*)gate != gate_want) return;
+    dgemm_tile(g, blockIdx.x);
+}
+
 // orth = max |G - I| over the n x n FP32 Gram; atomicMax on the float bit pattern (>= 0).
 __global__ void k_orth_max(int n, const float* __restrict__ G, DevState* st, unsigned int* bits)
 {
@@ -587,8 +594,8 @@ static int launch_apply_q(mpjsvd_ctx* h, int mrows, int ncols, int k, const doub
 
 static int launch_gemm_d(mpjsvd_ctx* h, const GemmArgs& g, const int* gate, int want)
 {
-    int tiles = ((g.M + kGemmBM - 1) / kGemmBM) * ((g.N + kGemmBN - 1) / kGemmBN);
-    k_gemm<double><<<tiles, kGemmThreads, 0, h->stream>>>(g, gate, want); ++h->launch_count;
+    const int tiles = ((g.M + kDgBM - 1) / kDgBM) * ((g.N + kDgBN - 1) / kDgBN);
+    k_dgemm<<<tiles, kDgThreads, 0, h->stream>>>(g, gate, want);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("gemm launch", e);
     ++h->launch_count;

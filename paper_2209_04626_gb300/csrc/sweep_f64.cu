@@ -9,7 +9,7 @@ static int try_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevS
 {
 #define MPJ_L(WW, RR) \
     if (w == WW && rpt == RR) return launch_sweeps_wr<double, true, WW, RR>(h, D, X, V, st, phase, gate_want, threads)
-    MPJ_L(1, 2); MPJ_L(1, 4); MPJ_L(1, 8); MPJ_L(1, 16);
+    MPJ_L(1, 2); MPJ_L(1, 4); MPJ_L(1, 8); MPJ_L(1, 16); MPJ_L(1, 32);
     MPJ_L(2, 2); MPJ_L(2, 4); MPJ_L(2, 8); MPJ_L(2, 16);
     MPJ_L(4, 2); MPJ_L(4, 4); MPJ_L(4, 8);
     MPJ_L(8, 2); MPJ_L(8, 4);
@@ -23,7 +23,7 @@ static int max_threads_f64(int w, int rpt)
     cudaFuncAttributes fa;
 #define MPJ_Q(WW, RR) \
     if (w == WW && rpt == RR) return cudaFuncGetAttributes(&fa, k_sweeps<double, true, WW, RR>) == cudaSuccess ? fa.maxThreadsPerBlock : 0
-    MPJ_Q(1, 2); MPJ_Q(1, 4); MPJ_Q(1, 8); MPJ_Q(1, 16);
+    MPJ_Q(1, 2); MPJ_Q(1, 4); MPJ_Q(1, 8); MPJ_Q(1, 16); MPJ_Q(1, 32);
     MPJ_Q(2, 2); MPJ_Q(2, 4); MPJ_Q(2, 8); MPJ_Q(2, 16);
     MPJ_Q(4, 2); MPJ_Q(4, 4); MPJ_Q(4, 8);
     MPJ_Q(8, 2); MPJ_Q(8, 4);
@@ -36,7 +36,7 @@ static int max_threads_f64(int w, int rpt)
 int sweep_fit_w_f64(int mX, int w_want)
 {
     for (int w = w_want; w >= 1; w /= 2)
-        for (int rpt = 2; rpt <= 16 && w * rpt <= 32; rpt *= 2) {
+        for (int rpt = 2; rpt <= 32 && w * rpt <= 32; rpt *= 2) {
             const int need = (mX + rpt - 1) / rpt;
             if (need > 1024) continue;
             const int mt = max_threads_f64(w, rpt);
@@ -54,7 +54,7 @@ int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, D
     const int w = D.w;
     int rpt = sweep_rpt(D.mX, w >= 8 ? 4 : 8);
     while (w * rpt > 32 && rpt > 2) rpt /= 2;
-    for (; rpt <= 16 && w * rpt <= 32; rpt *= 2) {
+    for (; rpt <= 32 && w * rpt <= 32; rpt *= 2) {
         if ((D.mX + rpt - 1) / rpt > 1024) continue;
         const int threads = sweep_threads(D.mX, rpt);
         int rc = try_f64(h, D, X, V, st, phase, gate_want, w, rpt, threads);
