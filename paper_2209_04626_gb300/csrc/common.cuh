@@ -42,7 +42,7 @@ struct DevState {
     unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
     unsigned long long amax_bits;          // Alg. 5: max |a_ij| (bits of a non-negative double)
-    float4 cand_sc[512];                   // Alg. 5: candidate's (alpha, |tail|, |col|) x parity
+    unsigned long long cand_rec[512];      // Alg. 5: per-CTA step records (tag, column, norm) x parity
 };
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative

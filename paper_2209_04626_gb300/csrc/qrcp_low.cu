@@ -8,9 +8,11 @@
 // the binary32 digits. Every norm is taken on power-of-two scaled entries, so the squares of
 // small columns do not underflow (the convention of single-precision LAPACK norms).
 //
-// One cooperative launch; CTA r owns the columns r, r + G, ... resident in shared memory.
-// Each step publishes every CTA's candidate (norm, column) and the candidate's rows in one
-// slot, then one grid barrier: every CTA then reads the winner's column from its slot.
+// Shared-memory kernel: one cooperative launch; CTA r owns the columns r, r + G, ... resident
+// in shared memory. Each step publishes every CTA's candidate (norm, column) and the
+// candidate's rows in one slot, then one grid barrier: every CTA then reads the winner's
+// column from its slot. The register-resident kernel below replaces the barrier by per-CTA
+// step records.
 #include "common.cuh"
 #include "internal.h"
 #include "qr.cuh"
@@ -87,6 +89,12 @@ __global__ void __launch_bounds__(kLowThreads)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
     if (lane == 0) atomicMax(&st->amax_bits, (unsigned long long)__double_as_longlong(am));
+    // slot of (parity, CTA r): m row words, then alpha, |tail|, |column|
+    unsigned long long* const llb = reinterpret_cast<unsigned long long*>(bcast);
+    const size_t slot_words = (size_t)m + 4;
+    if (tid < 2) st->cand_rec[tid * kQrSlotStride + g.rank] = 0ull;  // no step tag yet
+    for (size_t i = tid; i < 2 * slot_words; i += blockDim.x)
+        llb[((i / slot_words) * g.size + g.rank) * slot_words + i % slot_words] = 0ull;
     if (!g.sync()) return;
     if (tid == 0) s_amax = __longlong_as_double((long long)__ldcg(&st->amax_bits));
     __syncthreads();
@@ -237,18 +245,52 @@ __global__ void __launch_bounds__(kLowThreads)
 
 // ------------------------------------------------------------------------------------------
 // Register-resident variant: warp w of CTA b owns column c = 8 b + w, its rows lane + 32 k
-// (k < KR) in registers, so applying a reflector is warp-local (no CTA barrier). Before each
-// grid barrier the CTA's candidate warp publishes its rows j.. and the reflector's scalars
-// (alpha, |tail|, |column|, computed exactly from its registers), so after the barrier every
-// CTA has the step's reflector without a reduction. Same pivot rule, downdating and norms as
-// the kernel above.
+// (k < KR) in registers, so applying a reflector is warp-local (no CTA barrier).
+//
+// Exchange without barriers or fences. Every word a CTA publishes in step j is 64 bits wide
+// and carries the tag j + 1 in its upper half, so a reader that sees the tag sees the value
+// (an aligned 8-byte access is single-copy atomic), whatever order the writer's stores land
+// in. In step j the CTA's candidate warp writes its rows j.. and the reflector's scalars
+// (alpha, |tail|, |column|, computed exactly from its registers) to its slot, then the record
+// {tag, column, norm}. Warp 0 of every CTA polls the G records of step j until all carry the
+// tag, takes the argmax; then each thread reads its rows of the winner's slot, re-reading a
+// word until its tag is j + 1. A CTA cannot publish step j + 2 (same slot parity as j) before
+// every CTA has published step j + 1, i.e. has finished reading step j, so two slot sets
+// suffice; each CTA clears its slots and records before the one grid barrier at the start,
+// so words of an earlier call never carry a tag of this one. Same pivot rule, downdating and
+// norms as the kernel above.
 constexpr int kRegWarps = 8;
+
+// record of CTA candidate (column c, norm v >= 0) for step j; none: c = 0xffff
+__device__ __forceinline__ unsigned long long cand_record(int j, int c, float v)
+{
+    return ((unsigned long long)((j + 1) & 0xffff) << 48) | ((unsigned long long)(c & 0xffff) << 32) |
+           (unsigned long long)__float_as_uint(v);
+}
+// tagged word of step j: {value, j + 1}
+__device__ __forceinline__ unsigned long long tagged(float v, int j)
+{
+    return ((unsigned long long)(unsigned)(j + 1) << 32) | (unsigned long long)__float_as_uint(v);
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Phase probes of the register-resident kernel: empty here; a profiling build may define them.
 #ifndef MPJ_QRCP_PROBE_BEGIN
 #define MPJ_QRCP_PROBE_BEGIN
 #define MPJ_QRCP_PROBE(i)
 #define MPJ_QRCP_PROBE_END
+#endif
+#ifndef MPJ_QRCP_MARK
+#define MPJ_QRCP_MARK(k, j, extra) {}
 #endif
 
 template <int KR>
@@ -274,6 +316,52 @@ __device__ __forceinline__ float reg_norm_scaled(const float (&x)[KR], int lo, i
     return sqrtf(s) / sc;
 }
 
+// Reflector scalars of the candidate column in one pass over the registers: |x(j+1:m)| on
+// entries scaled by the power of two of its own maximum, and |x(j:m)| from it and alpha =
+// x(j) (both on power-of-two scaled values, so no square underflows or overflows). Four
+// independent chains per lane; the maximum is one redux (non-negative binary32 values order
+// like their bit patterns).
+template <int KR>
+__device__ __forceinline__ void reg_cand_scalars(const float (&x)[KR], int j, int lane, float alpha, float& tailn,
+                                                 float& nrm)
+{
+    unsigned mb[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        if (lane + 32 * k > j) mb[k & 3] = max(mb[k & 3], __float_as_uint(fabsf(x[k])));
+    const unsigned mt = __reduce_max_sync(0xffffffffu, max(max(mb[0], mb[1]), max(mb[2], mb[3])));
+    const float aa = fabsf(alpha);
+    if (mt == 0u) {
+        tailn = 0.0f;
+        nrm = aa;
+        return;
+    }
+    const int et = (int)(mt >> 23) & 0xff;
+    const float sct = __int_as_float((254 - et) << 23);  // max |tail| * sct in [1, 2)
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        if (lane + 32 * k > j) {
+            const float y = x[k] * sct;
+            s[k & 3] = fmaf(y, y, s[k & 3]);
+        }
+    const float st = warp_sum((s[0] + s[1]) + (s[2] + s[3]));
+    tailn = sqrtf(st) / sct;
+    const int ea = (int)(__float_as_uint(aa) >> 23) & 0xff;
+    if (ea <= et) {
+        const float ya = alpha * sct;
+        nrm = sqrtf(fmaf(ya, ya, st)) / sct;
+    } else {
+        // |alpha| is the larger: scale by its power of two; the tail's sum moves by an exact
+        // power of two (its square, 2^(2 (et - ea)))
+        const float sca = __int_as_float((254 - ea) << 23);
+        const float ya = alpha * sca;
+        const int d = et - ea;  // < 0
+        const float r2 = (2 * d >= -149) ? ldexpf(1.0f, 2 * d) : 0.0f;
+        nrm = sqrtf(fmaf(st, r2, ya * ya)) / sca;
+    }
+}
+
 // the entry of row r (all lanes receive it)
 template <int KR>
 __device__ __forceinline__ float reg_row(const float (&x)[KR], int r, int lane)
@@ -296,7 +384,7 @@ __global__ void __launch_bounds__(kRegWarps * 32)
     __shared__ int wcol[kRegWarps];
     __shared__ double s_amax;
     __shared__ int s_piv;
-    __shared__ float4 s_sc;
+    __shared__ float s_scal[3];
     if (call_failed(st)) return;
     const Group g{(int)blockIdx.x, (int)gridDim.x, st};
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -311,6 +399,12 @@ __global__ void __launch_bounds__(kRegWarps * 32)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
     if (lane == 0) atomicMax(&st->amax_bits, (unsigned long long)__double_as_longlong(am));
+    // slot of (parity, CTA r): m row words, then alpha, |tail|, |column|
+    unsigned long long* const llb = reinterpret_cast<unsigned long long*>(bcast);
+    const size_t slot_words = (size_t)m + 4;
+    if (tid < 2) st->cand_rec[tid * kQrSlotStride + g.rank] = 0ull;  // no step tag yet
+    for (size_t i = tid; i < 2 * slot_words; i += blockDim.x)
+        llb[((i / slot_words) * g.size + g.rank) * slot_words + i % slot_words] = 0ull;
     if (!g.sync()) return;
     if (tid == 0) s_amax = __longlong_as_double((long long)__ldcg(&st->amax_bits));
     __syncthreads();
@@ -328,75 +422,94 @@ __global__ void __launch_bounds__(kRegWarps * 32)
     MPJ_QRCP_PROBE_BEGIN
 
     const int kmax = min(m, n);
+    if (lane == 0) {
+        wvn[wid] = act ? vn1 : -1.0f;
+        wcol[wid] = act ? c : -1;
+    }
+    __syncthreads();
     for (int j = 0; j < kmax; ++j) {
+        const int par = j & 1;
         // ---- this CTA's candidate (first maximum in column order) publishes itself
-        if (lane == 0) {
-            wvn[wid] = act ? vn1 : -1.0f;
-            wcol[wid] = act ? c : -1;
-        }
-        __syncthreads();
         MPJ_QRCP_PROBE(0)
+        if (tid == 0) MPJ_QRCP_MARK(0, j, 0)
         int cw = -1;
         float cv = 0.0f;
 #pragma unroll
         for (int w = 0; w < kRegWarps; ++w)
             if (wcol[w] >= 0 && (cw < 0 || wvn[w] > cv)) { cv = wvn[w]; cw = w; }
         if (wid == cw) {
-            float* slot = bcast + ((size_t)(j & 1) * g.size + g.rank) * m;
+            // rows, then scalars, then the record: a reader that sees the record rarely has
+            // to wait for the rest
+            unsigned long long* slot = llb + ((size_t)par * g.size + g.rank) * slot_words;
 #pragma unroll
             for (int k = 0; k < KR; ++k) {
                 const int i = lane + 32 * k;
-                if (i >= j && i < m) slot[i] = x[k];
+                if (i > j && i < m) st_relaxed_u64(slot + i, tagged(x[k], j));
             }
             const float alpha = reg_row<KR>(x, j, lane);
-            const float tailn = reg_norm_scaled<KR>(x, j + 1, lane);
-            const float nrm = reg_norm_scaled<KR>(x, j, lane);
-            if (lane == 0) {
-                put_candidate(st, j & 1, g.rank, (double)cv, c);
-                st->cand_sc[(j & 1) * kQrSlotStride + g.rank] = make_float4(alpha, tailn, nrm, 0.0f);
-            }
+            float tailn, nrm;
+            reg_cand_scalars<KR>(x, j, lane, alpha, tailn, nrm);
+            if (lane < 3) st_relaxed_u64(slot + m + lane, tagged(lane == 0 ? alpha : (lane == 1 ? tailn : nrm), j));
+            if (lane == 0) st_relaxed_u64(&st->cand_rec[par * kQrSlotStride + g.rank], cand_record(j, c, cv));
+            if (lane == 0) MPJ_QRCP_MARK(1, j, 0)
         } else if (cw < 0 && tid == 0) {
-            put_candidate(st, j & 1, g.rank, 0.0, -1);
+            st_relaxed_u64(&st->cand_rec[par * kQrSlotStride + g.rank], cand_record(j, 0xffff, 0.0f));
         }
         MPJ_QRCP_PROBE(1)
-        if (!g.sync()) return;
-        MPJ_QRCP_PROBE(2)
         if (wid == 0) {
-            // argmax over the candidates with every CTA's scalars loaded in the same pass
+            // wait for the G records of step j (lane l holds records l, l + 32, ...)
             constexpr int K = kQrSlotStride / 32;
-            double2 cd[K];
-            float4 sc[K];
+            const unsigned want = (unsigned)((j + 1) & 0xffff);
+            unsigned long long rec[K];
+#pragma unroll
+            for (int q = 0; q < K; ++q) rec[q] = 0ull;
+            const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            bool ready = false;
+            while (true) {
+                bool mine = true;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r < g.size && (unsigned)(rec[q] >> 48) != want)
+                        rec[q] = ld_relaxed_u64(&st->cand_rec[par * kQrSlotStride + r]);
+                }
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r < g.size && (unsigned)(rec[q] >> 48) != want) mine = false;
+                }
+                if (__all_sync(0xffffffffu, mine)) {
+                    ready = true;
+                    break;
+                }
+                if ((++spins & 255u) == 0) {
+                    if (*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) break;
+                    if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                        if (lane == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            if (lane == 0) MPJ_QRCP_MARK(2, j, spins)
+            // argmax: largest norm, then the lowest column index (key order)
+            unsigned long long best = 0ull;
 #pragma unroll
             for (int q = 0; q < K; ++q) {
                 const int r = lane + 32 * q;
-                cd[q] = (r < g.size) ? __ldcg(&st->cand[(j & 1) * kQrSlotStride + r]) : make_double2(0.0, -1.0);
-                sc[q] = (r < g.size) ? __ldcg(&st->cand_sc[(j & 1) * kQrSlotStride + r]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            int best = -1;
-            double bv = 0.0;
-            float4 bs = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const int idx = (int)cd[q].y;
-                if (idx >= 0 && (best < 0 || cd[q].x > bv || (cd[q].x == bv && idx < best))) {
-                    bv = cd[q].x; best = idx; bs = sc[q];
+                const unsigned cidx = (unsigned)(rec[q] >> 32) & 0xffffu;
+                if (r < g.size && cidx != 0xffffu) {
+                    const unsigned long long key = ((rec[q] & 0xffffffffull) << 32) | 0x80000000ull |
+                                                   (unsigned long long)(0xffffu - cidx);
+                    best = key > best ? key : best;
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, best, o);
-                const float ox = __shfl_xor_sync(0xffffffffu, bs.x, o);
-                const float oy = __shfl_xor_sync(0xffffffffu, bs.y, o);
-                const float oz = __shfl_xor_sync(0xffffffffu, bs.z, o);
-                if (oi >= 0 && (best < 0 || ov > bv || (ov == bv && oi < best))) {
-                    bv = ov; best = oi; bs = make_float4(ox, oy, oz, 0.f);
-                }
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                best = ob > best ? ob : best;
             }
-            if (lane == 0) {
-                s_piv = best;
-                s_sc = bs;
-            }
+            if (lane == 0) s_piv = (ready && best != 0ull) ? (int)(0xffffu - (unsigned)(best & 0xffffu)) : -1;
         }
         __syncthreads();
         const int p = s_piv;
@@ -404,20 +517,66 @@ __global__ void __launch_bounds__(kRegWarps * 32)
             if (tid == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
             return;
         }
+        MPJ_QRCP_PROBE(2)
         MPJ_QRCP_PROBE(3)
         const int pb = p / kRegWarps;  // the winner's CTA
-        const float alpha = s_sc.x, tailn = s_sc.y, nrm = s_sc.z;
+        const unsigned long long* src = llb + ((size_t)par * g.size + pb) * slot_words;
+        constexpr int kFill = (32 * KR + kRegWarps * 32 - 1) / (kRegWarps * 32);
+        const unsigned want = (unsigned)(j + 1);
+        unsigned long long wv[kFill + 1];  // this thread's rows of the winner (+ one scalar for tid < 3)
+#pragma unroll
+        for (int q = 0; q < kFill + 1; ++q) wv[q] = 0ull;
+        const bool has_sc = tid < 3;  // threads 0..2 fetch alpha, |tail|, |column| for the CTA
+        bool bad = false;
+        {
+            const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (true) {
+                // issue every pending load, then check (no load waits on another)
+#pragma unroll
+                for (int q = 0; q < kFill; ++q) {
+                    const int i = j + 1 + tid + q * kRegWarps * 32;
+                    if (i < m && (unsigned)(wv[q] >> 32) != want) wv[q] = ld_relaxed_u64(src + i);
+                }
+                if (has_sc && (unsigned)(wv[kFill] >> 32) != want) wv[kFill] = ld_relaxed_u64(src + m + tid);
+                bool ok = !(has_sc && (unsigned)(wv[kFill] >> 32) != want);
+#pragma unroll
+                for (int q = 0; q < kFill; ++q) {
+                    const int i = j + 1 + tid + q * kRegWarps * 32;
+                    if (i < m && (unsigned)(wv[q] >> 32) != want) ok = false;
+                }
+                if (ok) break;
+                if ((++spins & 255u) == 0) {
+                    if ((*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) ||
+                        globaltimer_ns() - t0 > kSpinLimitNs) {
+                        bad = true;
+                        break;
+                    }
+                }
+            }
+        }
+        if (has_sc) s_scal[tid] = __uint_as_float((unsigned)wv[kFill]);
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+            return;
+        }
+        const float alpha = s_scal[0], tailn = s_scal[1], nrm = s_scal[2];
         float tj = 0.0f, den = 1.0f;
         if (tailn != 0.0f) {
             const float beta = (alpha >= 0.0f) ? -nrm : nrm;
             tj = (beta - alpha) / beta;
             den = alpha - beta;
         }
-        const float* src = bcast + ((size_t)(j & 1) * g.size + pb) * m;
-        if (tj != 0.0f)
-            for (int i = j + 1 + tid; i < m; i += blockDim.x) vs[i] = __ldcg(src + i) / den;
+        if (tj != 0.0f) {
+#pragma unroll
+            for (int q = 0; q < kFill; ++q) {
+                const int i = j + 1 + tid + q * kRegWarps * 32;
+                if (i < m) vs[i] = __uint_as_float((unsigned)wv[q]) / den;
+            }
+        }
         __syncthreads();
         MPJ_QRCP_PROBE(4)
+        if (tid == 0) MPJ_QRCP_MARK(4, j, 0)
 
         // ---- apply H_j to this warp's column, downdate its norm
         if (act && c == p) {
@@ -425,13 +584,13 @@ __global__ void __launch_bounds__(kRegWarps * 32)
             if (lane == 0) perm[j] = p;
         } else if (act) {
             if (tj != 0.0f) {
-                float d = 0.0f;
+                float dp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int k = 0; k < KR; ++k) {
                     const int i = lane + 32 * k;
-                    if (i > j && i < m) d = fmaf(vs[i], x[k], d);
+                    if (i > j && i < m) dp[k & 3] = fmaf(vs[i], x[k], dp[k & 3]);
                 }
-                d = warp_sum(d);
+                const float d = warp_sum((dp[0] + dp[1]) + (dp[2] + dp[3]));
                 const float w = tj * (reg_row<KR>(x, j, lane) + d);
 #pragma unroll
                 for (int k = 0; k < KR; ++k) {
@@ -454,7 +613,13 @@ __global__ void __launch_bounds__(kRegWarps * 32)
             }
         }
         MPJ_QRCP_PROBE(5)
-        __syncthreads();  // wvn / wcol and vs are rewritten by the next step
+        if (tid == 0) MPJ_QRCP_MARK(5, j, 0)
+        if (lane == 0) {
+            wvn[wid] = act ? vn1 : -1.0f;
+            wcol[wid] = act ? c : -1;
+        }
+        // the next step reads wvn / wcol; vs is rewritten only after its pivot barrier
+        __syncthreads();
         MPJ_QRCP_PROBE(6)
     }
     MPJ_QRCP_PROBE_END

@@ -126,6 +126,25 @@ __device__ __forceinline__ void rot_params<double>(double alpha, double beta, do
     ic = q1 * c;
 }
 
+// binary32 variant (the lower-precision stage): the reciprocal by the fast division
+// intrinsic (a tangent off by a few ulps only changes how completely the pair is
+// annihilated); the cosine is rsqrtf(1 + t^2) for that t, orthogonal to binary32 precision.
+template <>
+__device__ __forceinline__ void rot_params<float>(float alpha, float beta, float gamma, float& t, float& c,
+                                                  float& ic)
+{
+    const float dd = beta - alpha, g2 = 2.0f * gamma;
+    const float sc = pow2_down(dd, g2);
+    const float ds = dd * sc, gs = g2 * sc;
+    const float D2 = fmaf(ds, ds, gs * gs);
+    const float D = D2 * rsqrtf(D2);
+    const float num = (dd == 0.0f) ? fabsf(gs) : ((dd > 0.0f) ? gs : -gs);
+    t = __fdividef(num, fabsf(ds) + D);
+    const float q1 = fmaf(t, t, 1.0f);
+    c = rsqrtf(q1);
+    ic = q1 * c;
+}
+
 // True when x <= 0 or x < y / 16 up to a factor of two (y > 0), from the sign and binary
 // exponents (no floating-point instruction): flags a tracked norm that lost about four bits
 // to cancellation.
