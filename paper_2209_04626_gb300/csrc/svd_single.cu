@@ -515,10 +515,12 @@ static int pick_w(int n, int mX, bool low, int sms, int forced)
     } else if (low) {
         w = 8;
     } else {
-        // narrowest power of two that still leaves >= 1.5 visits per SM in every round, so
-        // that two or more CTAs share each SM and hide each other's latency-bound steps
+        // narrowest power of two that leaves fewer than 0.75 visits per SM in a round: a
+        // sweep is a chain of n / w - 1 rounds, so wider blocks shorten it, while the visits
+        // of a round (and of the next rounds, released as their blocks arrive) still cover
+        // the SMs (1024 columns: w = 4, 128 visits per round)
         w = 1;
-        while ((double)n / (4.0 * w) >= 1.5 * sms) w *= 2;
+        while ((double)n / (4.0 * w) >= 0.75 * sms) w *= 2;
         if (n <= 512) w = std::max(w, 8);  // small n: latency bound, fewer rounds win
     }
     w = std::min(w, std::min(wmax, smem_cap));

@@ -47,12 +47,14 @@ int sweep_fit_w_f64(int mX, int w_want)
 
 // Block width w in {1, 2, 4, 8}; rows per thread chosen so that the visit's 2w columns fit
 // in registers (w * rpt <= 32 doubles per thread), doubled while a variant's register use
-// does not allow the thread count.
+// does not allow the thread count. Four rows per thread from w = 4 up (measured on the
+// 1024-column refinement: w = 4 with 256 threads 25.6 ms, with 128 threads 27.9 ms, with 512
+// threads 29.3 ms; w = 2 with 128 threads 27.6 ms).
 int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
                       int phase, int gate_want, int* threads_out)
 {
     const int w = D.w;
-    int rpt = sweep_rpt(D.mX, w >= 8 ? 4 : 8);
+    int rpt = sweep_rpt(D.mX, w >= 4 ? 4 : 8);
     while (w * rpt > 32 && rpt > 2) rpt /= 2;
     for (; rpt <= 32 && w * rpt <= 32; rpt *= 2) {
         if ((D.mX + rpt - 1) / rpt > 1024) continue;
