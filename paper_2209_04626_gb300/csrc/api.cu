@@ -105,11 +105,20 @@ int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream)
     c->have_events = true;
     for (int i = 0; i < 8; ++i)
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
-    c->have_side = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
-    for (int i = 0; i < 5 && c->have_side; ++i)
+    // look-ahead streams: when both CTAs of the critical chain and of a wide update are
+    // waiting for an SM, the critical chain's go first
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    c->have_side = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) == cudaSuccess;
+    if (c->have_side && cudaStreamCreateWithPriority(&c->crit, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+        cudaStreamDestroy(c->side);
+        c->have_side = false;
+    }
+    for (int i = 0; i < 7 && c->have_side; ++i)
         if (cudaEventCreateWithFlags(&c->qev[i], cudaEventDisableTiming) != cudaSuccess) {
             for (int k = 0; k < i; ++k) cudaEventDestroy(c->qev[k]);
             cudaStreamDestroy(c->side);
+            cudaStreamDestroy(c->crit);
             c->have_side = false;
         }
     cudaGetLastError();  // a failed optional resource leaves no sticky error behind
@@ -246,8 +255,10 @@ int mpjsvd_destroy(mpjsvd_handle h)
     if (h->dstate) cudaFree(h->dstate);
     if (h->have_side) {
         cudaStreamSynchronize(h->side);
-        for (int i = 0; i < 5; ++i) cudaEventDestroy(h->qev[i]);
+        cudaStreamSynchronize(h->crit);
+        for (int i = 0; i < 7; ++i) cudaEventDestroy(h->qev[i]);
         cudaStreamDestroy(h->side);
+        cudaStreamDestroy(h->crit);
     }
     if (h->have_events)
         for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);

@@ -31,9 +31,13 @@ struct mpjsvd_ctx {
     int last_block_w_low, last_block_w_work;
     int launch_count;  // kernels launched by the last call
     int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
-    // second stream for the blocked QR's look-ahead (fork/join through events on `stream`)
-    cudaStream_t side;
-    cudaEvent_t qev[5];  // [0] panel done, [1..3] wide updates (ring), [4] join
+    // the blocked QR's look-ahead: the critical chain (panels and the updates of the next
+    // panel) on a high-priority stream, the wide trailing updates on a low-priority one;
+    // both fork from and join back into `stream` through events
+    cudaStream_t side;   // lowest priority: wide updates
+    cudaStream_t crit;   // highest priority: panels and narrow updates
+    cudaEvent_t qev[7];  // [0] panel done, [1..3] wide updates (ring), [4] side join,
+                         // [5] fork, [6] critical-chain join
     bool have_side;
 };
 

@@ -41,7 +41,8 @@ namespace mpj {
 
 constexpr int kPanelCl = 8;        // CTAs per panel cluster (portable cluster size)
 constexpr int kPanelThreads = 256;
-constexpr int kWyRc = 128;         // rows per tile of the trailing kernels
+constexpr int kWyRc = 128;         // rows per tile of the wide trailing updates and of Q C
+constexpr int kWyRcNarrow = 32;    // rows per tile of the look-ahead's narrow (next panel) update
 constexpr int kWyThreads = 256;
 constexpr size_t kPanelSmemMax = 200 * 1024;
 
@@ -337,17 +338,20 @@ struct WySet {
 };
 constexpr int kWyMaxChunks = 32;
 
-// Partial W(k, c) = sum_r v_k(r) C(r, c0 + c) over row chunk blockIdx.y (spc tiles of kWyRc
+// Partial W(k, c) = sum_r v_k(r) C(r, c0 + c) over row chunk blockIdx.y (spc tiles of RC
 // rows) and the 32 columns of strip blockIdx.x; the strip after the last one forms the Gram
 // matrix V^T V. Each CTA stores its partial; the last CTA of a strip to finish (per-strip
 // counter) sums the partials in chunk order (the result does not depend on timing), and for
-// the Gram strip builds T.
-template <int NB>
+// the Gram strip builds T. Every CTA does RC * 32 * NB FMAs: narrow updates (on the
+// factorization's critical path) use short tiles so that more SMs share them.
+template <int NB, int RC>
 __global__ void __launch_bounds__(kWyThreads)
     k_wy_w(int m, int j0, int nbp, const double* V, int ldv, const double* C, int ldc, int c0,
            int ncols, int spc, WySet ws, const double* tau, DevState* st, int gate_want)
 {
-    __shared__ double Vs[NB][kWyRc + 1];
+    constexpr int kTile = NB * (RC + 1), kTsc = 3 * NB * (NB + 1);
+    __shared__ double Vsb[kTile > kTsc ? kTile : kTsc];  // the V tile, later T's scratch
+    double(*Vs)[RC + 1] = reinterpret_cast<double(*)[RC + 1]>(Vsb);
     __shared__ int s_last;
     if (gate_skip(st, gate_want)) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -371,15 +375,15 @@ __global__ void __launch_bounds__(kWyThreads)
 #pragma unroll
     for (int i = 0; i < CPT; ++i) acc[i] = 0.0;
     for (int sc = 0; sc < spc; ++sc) {
-        const int r0 = j0 + (blockIdx.y * spc + sc) * kWyRc;
+        const int r0 = j0 + (blockIdx.y * spc + sc) * RC;
         if (r0 >= m) break;
         __syncthreads();  // Vs of the previous tile is no longer read
-        for (int e = tid; e < NB * kWyRc; e += kWyThreads) {
-            const int kk = e / kWyRc, r = e % kWyRc, gr = r0 + r;
+        for (int e = tid; e < NB * RC; e += kWyThreads) {
+            const int kk = e / RC, r = e % RC, gr = r0 + r;
             Vs[kk][r] = (kk < nbp && gr < m) ? refl_at(V, ldv, j0, kk, gr) : 0.0;
         }
         __syncthreads();
-        const int rend = min(kWyRc, m - r0);
+        const int rend = min(RC, m - r0);
         for (int r = 0; r < rend; ++r) {
             const double v = Vs[k][r];
             const int gr = r0 + r;
@@ -412,29 +416,29 @@ __global__ void __launch_bounds__(kWyThreads)
     if (tid == 0) ws.cnt[strip] = 0u;
     if (!is_gram) return;
     __syncthreads();
-    static_assert(3 * NB * (NB + 1) <= NB * (kWyRc + 1), "T scratch must fit in the V tile");
-    double(*Ts)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(&Vs[0][0]);
+    double(*Ts)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(Vsb);
     double(*Gs)[NB + 1] = Ts + NB;
     double(*Ms)[NB + 1] = Ts + 2 * NB;
     build_T<NB>(ws.W + (size_t)ncols * NB, tau, j0, nbp, Ts, Gs, Ms);
     for (int e = tid; e < NB * NB; e += kWyThreads) ws.T[e] = Ts[e % NB][e / NB];
 }
 
-// C(r, c0 + c) -= sum_k v_k(r) W'(k, c), W' = op(T) W(:, strip), over a tile of kWyRc rows x
+// C(r, c0 + c) -= sum_k v_k(r) W'(k, c), W' = op(T) W(:, strip), over a tile of RC rows x
 // 32 columns; op(T) = T^T (trans: Q_panel^T C, the QR's trailing update) or T (Q_panel C).
-template <int NB>
+template <int NB, int RC>
 __global__ void __launch_bounds__(kWyThreads)
     k_wy_update(int m, int j0, int nbp, const double* V, int ldv, double* C, int ldc, int c0,
                 int ncols, const double* W, const double* T, bool trans, DevState* st, int gate_want)
 {
-    __shared__ double Vs[NB][kWyRc + 1];
+    static_assert(RC % 32 == 0, "rows per thread are lane + 32 i");
+    __shared__ double Vs[NB][RC + 1];
     __shared__ double Ws[NB][33];
     if (gate_skip(st, gate_want)) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int r0 = j0 + blockIdx.y * kWyRc;
+    const int r0 = j0 + blockIdx.y * RC;
     const int cs = blockIdx.x * 32;
-    for (int e = tid; e < NB * kWyRc; e += kWyThreads) {
-        const int k = e / kWyRc, r = e % kWyRc, gr = r0 + r;
+    for (int e = tid; e < NB * RC; e += kWyThreads) {
+        const int k = e / RC, r = e % RC, gr = r0 + r;
         Vs[k][r] = (k < nbp && gr < m) ? refl_at(V, ldv, j0, k, gr) : 0.0;
     }
     for (int e = tid; e < NB * 32; e += kWyThreads) {
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(kWyThreads)
         for (int q = 0; q < KPT; ++q) Ws[ks[q]][lane] = out[q];
         __syncthreads();
     }
-    constexpr int RI = kWyRc / 32;              // rows per thread (lane + 32 i)
+    constexpr int RI = RC / 32;                 // rows per thread (lane + 32 i)
     constexpr int CJ = 32 / (kWyThreads / 32);  // columns per thread (wid * CJ + j)
     double acc[RI][CJ];
     bool rok[RI], cok[CJ];
@@ -519,23 +523,24 @@ int bqr_nb(int m)
     return 0;
 }
 
-// Row chunks of a step with m - j0 <= m_max rows (at most kWyMaxChunks).
-static int wy_chunks_max(int m_max) { return std::max(1, std::min(kWyMaxChunks, (m_max + kWyRc - 1) / kWyRc)); }
+// Row chunks of a step with m - j0 <= m_max rows and tiles of rc rows (at most kWyMaxChunks).
+static int wy_chunks_max(int m_max, int rc) { return std::max(1, std::min(kWyMaxChunks, (m_max + rc - 1) / rc)); }
 
-// Doubles of one accumulator set for up to ncap columns and m_max rows (sized for NB = 32).
-static size_t wyset_doubles(int ncap, int m_max)
+// Doubles of one accumulator set for up to ncap columns, m_max rows and tiles of rc rows
+// (sized for NB = 32).
+static size_t wyset_doubles(int ncap, int m_max, int rc)
 {
     const size_t ns = (size_t)(ncap + 31) / 32 + 1;
-    return (size_t)32 * ((size_t)ncap + 32) + 32 * 32 + (size_t)wy_chunks_max(m_max) * ns * 32 * 32 + (ns + 1) / 2 + 2;
+    return (size_t)32 * ((size_t)ncap + 32) + 32 * 32 + (size_t)wy_chunks_max(m_max, rc) * ns * 32 * 32 + (ns + 1) / 2 + 2;
 }
-static WySet wyset_at(double* base, int ncap, int m_max)
+static WySet wyset_at(double* base, int ncap, int m_max, int rc)
 {
     const size_t ns = (size_t)(ncap + 31) / 32 + 1;
     WySet w;
     w.W = base;
     w.T = w.W + (size_t)32 * ((size_t)ncap + 32);
     w.Wp = w.T + 32 * 32;
-    w.cnt = (unsigned*)(w.Wp + (size_t)wy_chunks_max(m_max) * ns * 32 * 32);
+    w.cnt = (unsigned*)(w.Wp + (size_t)wy_chunks_max(m_max, rc) * ns * 32 * 32);
     return w;
 }
 static size_t wyset_cnt_bytes(int ncap) { return sizeof(unsigned) * ((size_t)(ncap + 31) / 32 + 1); }
@@ -543,36 +548,39 @@ static size_t wyset_cnt_bytes(int ncap) { return sizeof(unsigned) * ((size_t)(nc
 // a narrow set (the next panel's columns) and a wide set (the rest / a whole apply)
 size_t bqr_wbuf_doubles(int ncols_max, int m_max)
 {
-    return wyset_doubles(32, m_max) + wyset_doubles(ncols_max, m_max);
+    return wyset_doubles(32, m_max, kWyRcNarrow) + wyset_doubles(ncols_max, m_max, kWyRc);
 }
 
 // One panel's compact-WY update C(j0:m, c0:c0+ncols) <- (I - V op(T) V^T) C with T built
 // from the panel's Gram matrix: op(T) = T^T applies Q_panel^T (QR trailing update), T applies
 // Q_panel (forming Q C). Rows are split into at most kWyMaxChunks chunks.
-template <int NB>
+template <int NB, int RC>
 static void wy_step(mpjsvd_ctx* h, cudaStream_t s, int m, int j0, int nbp, const double* V, int ldv,
                     const double* tau, double* C, int ldc, int c0, int ncols, const WySet& ws, bool trans,
                     DevState* st, int gate_want)
 {
     const int nstrips = (ncols + 31) / 32;
-    const int nsub = (m - j0 + kWyRc - 1) / kWyRc;
+    const int nsub = (m - j0 + RC - 1) / RC;
     const int spc = (nsub + kWyMaxChunks - 1) / kWyMaxChunks;
     const int nchunks = (nsub + spc - 1) / spc;
-    k_wy_w<NB><<<dim3(nstrips + 1, nchunks), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0, ncols, spc, ws,
-                                                                 tau, st, gate_want);
-    k_wy_update<NB><<<dim3(std::max(1, nstrips), nsub), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0,
-                                                                            ncols, ws.W, ws.T, trans, st,
-                                                                            gate_want);
+    k_wy_w<NB, RC><<<dim3(nstrips + 1, nchunks), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0, ncols, spc,
+                                                                     ws, tau, st, gate_want);
+    k_wy_update<NB, RC><<<dim3(std::max(1, nstrips), nsub), kWyThreads, 0, s>>>(m, j0, nbp, V, ldv, C, ldc, c0,
+                                                                                ncols, ws.W, ws.T, trans, st,
+                                                                                gate_want);
     h->launch_count += 2;
 }
 
 // Look-ahead: the panel after p needs only its own columns updated by panel p (the "narrow"
-// update, on the main stream), so the update of the columns beyond it (the "wide" update,
-// on the side stream) overlaps the factorization of the next panel. Column ranges:
-// panel p = [j0, j0 + nbp), next panel = [cn0, cn0 + nbn), wide = [cw0, n). Panel p's
-// columns have received every earlier update once wide(p-2) (side) and narrow(p-1) (main,
-// in order) are done; the narrow update of p needs wide(p-1). The narrow and wide updates
-// use separate accumulator sets; successive wide updates run in order on the side stream.
+// update), so the update of the columns beyond it (the "wide" update) overlaps the
+// factorization of the next panel. Panels and narrow updates form the critical chain and run
+// on the handle's high-priority stream, the wide updates on its low-priority stream: the
+// wide updates fill the GPU, and without the priorities the narrow update's CTAs queue
+// behind theirs (measured on 1024 x 1024: narrow 137 us per panel instead of ~10 us). Column
+// ranges: panel p = [j0, j0 + nbp), next panel = [cn0, cn0 + nbn), wide = [cw0, n). Panel
+// p's columns have received every earlier update once wide(p-2) and narrow(p-1) (in order
+// on the critical stream) are done; the narrow update of p needs wide(p-1). The narrow and
+// wide updates use separate accumulator sets; successive wide updates run in order.
 template <int NB>
 static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W,
                          DevState* st, int gate_want)
@@ -581,11 +589,15 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
     const size_t smax = sizeof(double) * NB * (size_t)(((m + kPanelCl - 1) / kPanelCl) | 1);
     cudaError_t e = cudaFuncSetAttribute(k_panel_qr<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (e != cudaSuccess) return cuda_fail("panel smem attribute", e);
-    const WySet wn = wyset_at(W, 32, m), ww = wyset_at(W + wyset_doubles(32, m), n, m);
+    const WySet wn = wyset_at(W, 32, m, kWyRcNarrow), ww = wyset_at(W + wyset_doubles(32, m, kWyRcNarrow), n, m, kWyRc);
     if ((e = cudaMemsetAsync(wn.cnt, 0, wyset_cnt_bytes(32), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(ww.cnt, 0, wyset_cnt_bytes(n), s)) != cudaSuccess)
         return cuda_fail("wy counters", e);
     const bool la = h->have_side;
+    const cudaStream_t c = la ? h->crit : s;
+    if (la && ((e = cudaEventRecord(h->qev[5], s)) != cudaSuccess || (e = cudaStreamWaitEvent(c, h->qev[5], 0)) != cudaSuccess ||
+               (e = cudaStreamWaitEvent(h->side, h->qev[5], 0)) != cudaSuccess))
+        return cuda_fail("blocked QR fork", e);
     int p = 0;
     for (int j0 = 0; j0 < n; j0 += NB, ++p) {
         const int nbp = std::min(NB, n - j0);
@@ -596,26 +608,29 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
             const int nt = n - cn0;
             k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, st, gate_want);
             ++h->launch_count;
-            if (nt > 0) wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nt, ww, true, st, gate_want);
+            if (nt > 0) wy_step<NB, kWyRc>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nt, ww, true, st, gate_want);
         } else {
-            if (p >= 2 && (e = cudaStreamWaitEvent(s, h->qev[1 + (p - 2) % 3], 0)) != cudaSuccess) break;
-            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, s>>>(m, j0, nbp, A, lda, tau, st, gate_want);
+            if (p >= 2 && (e = cudaStreamWaitEvent(c, h->qev[1 + (p - 2) % 3], 0)) != cudaSuccess) break;
+            k_panel_qr<NB><<<kPanelCl, kPanelThreads, psmem, c>>>(m, j0, nbp, A, lda, tau, st, gate_want);
             ++h->launch_count;
-            if ((e = cudaEventRecord(h->qev[0], s)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(h->qev[0], c)) != cudaSuccess) break;
             if ((e = cudaStreamWaitEvent(h->side, h->qev[0], 0)) != cudaSuccess) break;
-            if (ncw > 0) wy_step<NB>(h, h->side, m, j0, nbp, A, lda, tau, A, lda, cw0, ncw, ww, true, st, gate_want);
+            if (ncw > 0)
+                wy_step<NB, kWyRc>(h, h->side, m, j0, nbp, A, lda, tau, A, lda, cw0, ncw, ww, true, st, gate_want);
             if ((e = cudaEventRecord(h->qev[1 + p % 3], h->side)) != cudaSuccess) break;
             if (nbn > 0) {
-                if (p >= 1 && (e = cudaStreamWaitEvent(s, h->qev[1 + (p - 1) % 3], 0)) != cudaSuccess) break;
-                wy_step<NB>(h, s, m, j0, nbp, A, lda, tau, A, lda, cn0, nbn, wn, true, st, gate_want);
+                if (p >= 1 && (e = cudaStreamWaitEvent(c, h->qev[1 + (p - 1) % 3], 0)) != cudaSuccess) break;
+                wy_step<NB, kWyRcNarrow>(h, c, m, j0, nbp, A, lda, tau, A, lda, cn0, nbn, wn, true, st, gate_want);
             }
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
     }
-    if (la) {  // join: later work on the main stream sees every wide update
+    if (la) {  // join: later work on the handle's stream sees both chains
         cudaError_t e2 = cudaEventRecord(h->qev[4], h->side);
+        if (e2 == cudaSuccess) e2 = cudaEventRecord(h->qev[6], c);
         if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, h->qev[4], 0);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, h->qev[6], 0);
         if (e == cudaSuccess) e = e2;
     }
     if (e != cudaSuccess) return cuda_fail("blocked QR kernels", e);
@@ -641,7 +656,7 @@ int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, 
               double* C, int ldc, bool ident, double* W, DevState* st, int gate_want)
 {
     constexpr int NB = 32;
-    const WySet ws = wyset_at(W + wyset_doubles(32, m), ncols, m);
+    const WySet ws = wyset_at(W + wyset_doubles(32, m, kWyRcNarrow), ncols, m, kWyRc);
     cudaError_t e = cudaMemsetAsync(ws.cnt, 0, wyset_cnt_bytes(ncols), h->stream);
     if (e != cudaSuccess) return cuda_fail("wy counters", e);
     for (int j0 = ((k - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
@@ -649,7 +664,7 @@ int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, 
         const int cstart = ident ? j0 : 0;
         const int nc = ncols - cstart;
         if (nc <= 0) continue;
-        wy_step<NB>(h, h->stream, m, j0, nbp, V, ldv, tau, C, ldc, cstart, nc, ws, false, st, gate_want);
+        wy_step<NB, kWyRc>(h, h->stream, m, j0, nbp, V, ldv, tau, C, ldc, cstart, nc, ws, false, st, gate_want);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail("blocked apply kernels", e);
     }

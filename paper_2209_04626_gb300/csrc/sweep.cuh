@@ -161,6 +161,25 @@ __device__ __forceinline__ bool lost_bits(float x, float y)
     return ((bx >> 23) & 0xff) + 4 < ((__float_as_int(y) >> 23) & 0xff);
 }
 
+// The rotation test of Section 2.1, |gamma| > tol |x_a| |x_b|, from gamma and the squared
+// norms alpha = |x_a|^2, beta = |x_b|^2. binary32 takes the square roots: compared as squares,
+// alpha beta underflows once both columns are below about 1e-10 of unit size, and those pairs
+// would never be rotated (their directions would stay unresolved in the lower-precision
+// stage). binary64 compares squares, gamma^2 > tol^2 alpha beta (no square root on the scarce
+// FP64 pipe), which stays in range for column norms down to about 1e-75.
+template <typename T>
+__device__ __forceinline__ bool above_tol(T gamma, T al, T be, T tol, T tol2);
+template <>
+__device__ __forceinline__ bool above_tol<double>(double gamma, double al, double be, double, double tol2)
+{
+    return gamma * gamma > tol2 * (al * be);
+}
+template <>
+__device__ __forceinline__ bool above_tol<float>(float gamma, float al, float be, float tol, float)
+{
+    return fabsf(gamma) > tol * (sqrtf(al) * sqrtf(be));
+}
+
 // Sum of n >= 1 values with a dependency depth of about log2(4) + n / 4 instead of n.
 template <typename T>
 __device__ __forceinline__ T short_sum(const T* v, int n)
@@ -272,7 +291,7 @@ __device__ __forceinline__ void reg_norms(const T (&x)[RPT][2 * W], VisitShared<
 // One inner round (pairs given by intra/q), slot = its index in the visit's table.
 template <typename T, bool WITH_V, int W, int RPT>
 __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int q, int slot,
-                                            VisitShared<T, W>& sm, T tol2)
+                                            VisitShared<T, W>& sm, T tol, T tol2)
 {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int SH = 5 - ilog2c(W);
@@ -299,7 +318,7 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
             const T ia = sm.dinv[a], ib = sm.dinv[b];
             const T al = sm.alpha[a], be = sm.alpha[b];
             const T gamma = gh * (da * db);
-            if (gamma * gamma > tol2 * (al * be)) {  // |gamma| > tol |x_a| |x_b|
+            if (above_tol<T>(gamma, al, be, tol, tol2)) {
                 T t, c, ic;  // tangent, cosine and 1 / cosine of the rotation
                 rot_params(al, be, gamma, t, c, ic);
                 sm.tab[slot][p] = t * (db * ia);
@@ -398,7 +417,7 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
 {
     const int tid = threadIdx.x, nthr = blockDim.x;
     constexpr int W2 = 2 * W;
-    const T tol2 = T(D.tol * D.tol);  // the rotation test compares squares
+    const T tol1 = T(D.tol), tol2 = T(D.tol * D.tol);
     T* dsc = (T*)D.dsc;
     T* alph = (T*)D.alph;
     // fold a column into its data once its scale is this small (persistent scales only
@@ -443,11 +462,11 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
     // ---- inner rounds (unrolled: compile-time column indices)
     if (first) {
 #pragma unroll
-        for (int q = 0; q < W - 1; ++q) inner_round<T, WITH_V, W, RPT>(x, true, q, q, sm, tol2);
+        for (int q = 0; q < W - 1; ++q) inner_round<T, WITH_V, W, RPT>(x, true, q, q, sm, tol1, tol2);
     }
     const int base = first ? W - 1 : 0;
 #pragma unroll
-    for (int q = 0; q < W; ++q) inner_round<T, WITH_V, W, RPT>(x, false, q, base + q, sm, tol2);
+    for (int q = 0; q < W; ++q) inner_round<T, WITH_V, W, RPT>(x, false, q, base + q, sm, tol1, tol2);
 
     const int nrot = sm.flags[0];
     if (nrot > 0) {
