@@ -12,6 +12,7 @@ Prints one JSON line (rank 0). Timing: CUDA events on the library's stream aroun
 step, L2 flushed (256 MiB write) before every timed step, max over ranks.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -375,12 +376,17 @@ def ours(args):
             cpu = {"value": None, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
                    "sample": "failed: %s" % ex}
 
+    # DRAM bytes per launch of the refinement sweeps from an ncu capture; used only while the
+    # kernel's sources are the ones that were captured (their sha256 is recorded with it)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "sweep_fp64_traffic.json")
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
-            if tj.get("m") == m and tj.get("n") == n:
+            hh = hashlib.sha256()
+            for f in tj.get("sources", []):
+                hh.update(open(os.path.join(ROOT, f), "rb").read())
+            if tj.get("m") == m and tj.get("n") == n and hh.hexdigest() == tj.get("sources_sha256"):
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None
