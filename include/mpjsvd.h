@@ -60,6 +60,14 @@ extern "C" {
                                 default */
 #define MPJSVD_QRCP_F64 1    /* Businger-Golub QR with column pivoting in binary64 */
 
+/* params.stop: when Alg. 1 (both precisions) stops. */
+#define MPJSVD_STOP_XGESVJ 0 /* default: after a sweep without rotations, or after a sweep other
+                                than the first whose rotations were all negligible (largest
+                                cosine among the rotated pairs below sqrt(n) tol and n times it
+                                times the largest |tan| below tol): the rule of LAPACK's xGESVJ,
+                                with which the paper's experiments run Alg. 1 (Section 7.1) */
+#define MPJSVD_STOP_ALG1 1   /* only after a sweep without rotations (Alg. 1 as printed) */
+
 typedef struct mpjsvd_ctx* mpjsvd_handle;
 
 /* Tunables. Defaults (mpjsvd_default_params) are the paper's values of Section 7.1. */
@@ -78,6 +86,7 @@ typedef struct {
     int timing;           /* 1: record per-phase CUDA-event times in mpjsvd_stats */
     int qrcp;             /* MPJSVD_QRCP_*; Alg. 5 falls back to binary64 when the binary32
                              matrix does not fit the resident kernel (stats.qrcp tells) */
+    int stop;             /* MPJSVD_STOP_* */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */

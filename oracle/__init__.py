@@ -33,7 +33,8 @@ class _Variant:
         class Params(ctypes.Structure):
             _fields_ = [("tol_alg", creal), ("tol_orth", creal), ("tol_cond_coef", creal),
                         ("trailing_frac", creal), ("tol", creal), ("maxsweep", ctypes.c_int),
-                        ("mode", ctypes.c_int), ("precond", ctypes.c_int), ("qrcp", ctypes.c_int)]
+                        ("mode", ctypes.c_int), ("precond", ctypes.c_int), ("qrcp", ctypes.c_int),
+                        ("stop", ctypes.c_int)]
 
         class Stats(ctypes.Structure):
             _fields_ = [("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
@@ -59,10 +60,10 @@ class _Variant:
                                   ctypes.c_int, rp, rp, ctypes.c_int]
         L.orc_apply_q.restype = None
         L.orc_jacobi.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, ctypes.c_int,
-                                 ctypes.c_int, creal, ctypes.c_int, _ip,
+                                 ctypes.c_int, creal, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.POINTER(ctypes.c_longlong)]
         L.orc_jacobi_f32.argtypes = [ctypes.c_int, ctypes.c_int, _fp, ctypes.c_int, ctypes.c_float,
-                                     ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_longlong)]
+                                     ctypes.c_int, ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_longlong)]
         L.orc_rot_tangent.argtypes = [creal, creal, creal]
         L.orc_rot_tangent.restype = creal
         L.orc_svd.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, rp, rp,
@@ -182,8 +183,10 @@ def rot_tangent(alpha, beta, gamma, ext=False):
     return _v(ext).L.orc_rot_tangent(alpha, beta, gamma)
 
 
-def jacobi(X, V=None, tol=None, maxsweep=30, ext=False):
-    """Alg. 1 in the working precision on a copy of X; returns (X_inf, V, sweeps, rotations, rc)."""
+def jacobi(X, V=None, tol=None, maxsweep=30, ext=False, stop=0):
+    """Alg. 1 in the working precision on a copy of X; returns (X_inf, V, sweeps, rotations, rc).
+    stop: 0 also ends after a negligible sweep (the paper's experiments), 1 only after a sweep
+    without rotations (Alg. 1 as printed)."""
     v = _v(ext)
     X = v.arr(X).copy(order="F")
     m, n = X.shape
@@ -193,12 +196,12 @@ def jacobi(X, V=None, tol=None, maxsweep=30, ext=False):
     sw = ctypes.c_int()
     rot = ctypes.c_longlong()
     rc = v.L.orc_jacobi(m, n, v.ptr(X), m, v.ptr(V), V.shape[0] if V is not None else 1,
-                        V.shape[0] if V is not None else 0, tol, maxsweep, ctypes.byref(sw),
+                        V.shape[0] if V is not None else 0, tol, maxsweep, stop, ctypes.byref(sw),
                         ctypes.byref(rot))
     return X, V, sw.value, rot.value, rc
 
 
-def jacobi_f32(X, tol=None, maxsweep=30):
+def jacobi_f32(X, tol=None, maxsweep=30, stop=0):
     """Alg. 1 in binary32 without V; returns (X_inf, sweeps, rotations, rc)."""
     L = lib(False)
     X = np.asfortranarray(np.asarray(X, dtype=np.float32)).copy(order="F")
@@ -206,7 +209,7 @@ def jacobi_f32(X, tol=None, maxsweep=30):
     tol = np.sqrt(m) * 2.0 ** -24 if tol is None else tol
     sw = ctypes.c_int()
     rot = ctypes.c_longlong()
-    rc = L.orc_jacobi_f32(m, n, X.ctypes.data_as(_fp), m, tol, maxsweep, ctypes.byref(sw),
+    rc = L.orc_jacobi_f32(m, n, X.ctypes.data_as(_fp), m, tol, maxsweep, stop, ctypes.byref(sw),
                           ctypes.byref(rot))
     return X, sw.value, rot.value, rc
 

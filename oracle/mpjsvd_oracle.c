@@ -41,6 +41,7 @@ void orc_default_params(orc_params* p)
     p->mode = 0;
     p->precond = 0;
     p->qrcp = 0;
+    p->stop = 0;
 }
 
 static orc_real nrm2(int len, const orc_real* x)
@@ -300,16 +301,28 @@ orc_real orc_rot_tangent(orc_real alpha, orc_real beta, orc_real gamma)
     return (zeta >= 0.0) ? t : -t;
 }
 
+/* Stopping rule of the paper's experiments (Section 7.1 runs Alg. 1 as LAPACK's xGESVJ):
+ * besides a sweep without rotations, a sweep other than the first ends the iteration when
+ * every rotation in it was negligible: the largest cosine |x_p^T x_q| / (|x_p| |x_q|) among
+ * the rotated pairs is below sqrt(n) tol, and n times it times the largest |tan| of those
+ * rotations is below tol. */
+static int negligible_sweep(int n, double tol, double cos_max, double tan_max)
+{
+    return cos_max < sqrt((double)n) * tol && (double)n * cos_max * tan_max < tol;
+}
+
 /* Alg. 1 in binary64. Cyclic order (1,2),(1,3),...,(n-1,n) of eq. (cyclic). The pair
  * (p, q) is rotated when |x_q^T x_p| > tol |x_p| |x_q|; a sweep without rotations
- * means convergence. alpha, beta, gamma are recomputed from the columns for each pair. */
+ * means convergence (stop = 1), or also a negligible sweep (stop = 0, negligible_sweep).
+ * alpha, beta, gamma are recomputed from the columns for each pair. */
 int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
-               int maxsweep, int* sweeps, long long* rotations)
+               int maxsweep, int stop, int* sweeps, long long* rotations)
 {
     long long rot = 0;
     int sweep = 0, converged = 0;
     while (sweep < maxsweep && !converged) {
         converged = 1;
+        double cos_max = 0.0, tan_max = 0.0;
         for (int p = 0; p < n - 1; ++p) {
             for (int q = p + 1; q < n; ++q) {
                 orc_real* xp = &AT(X, 0, p, ldx);
@@ -322,6 +335,9 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
                 }
                 if (!(RFABS(gamma) > tol * RSQRT(alpha) * RSQRT(beta))) continue;
                 orc_real t = orc_rot_tangent(alpha, beta, gamma);
+                const double cs = (double)(RFABS(gamma) / (RSQRT(alpha) * RSQRT(beta)));
+                if (cs > cos_max) cos_max = cs;
+                if (fabs((double)t) > tan_max) tan_max = fabs((double)t);
                 orc_real c = 1.0 / RSQRT(1.0 + t * t);
                 orc_real s = c * t;
                 for (int i = 0; i < m; ++i) {
@@ -342,6 +358,8 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
                 converged = 0;
             }
         }
+        if (!converged && stop == 0 && sweep > 0 && negligible_sweep(n, (double)tol, cos_max, tan_max))
+            converged = 1;
         ++sweep;
     }
     if (sweeps) *sweeps = sweep;
@@ -349,15 +367,16 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
     return converged ? 0 : 1;
 }
 
-/* Alg. 1 in binary32 without V (the lower-precision stage of Alg. 4). Same steps as
- * orc_jacobi; every operation rounds to binary32. */
-int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int* sweeps,
+/* Alg. 1 in binary32 without V (the lower-precision stage of Alg. 4). Same steps and
+ * stopping rules as orc_jacobi; every operation rounds to binary32. */
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int stop, int* sweeps,
                    long long* rotations)
 {
     long long rot = 0;
     int sweep = 0, converged = 0;
     while (sweep < maxsweep && !converged) {
         converged = 1;
+        double cos_max = 0.0, tan_max = 0.0;
         for (int p = 0; p < n - 1; ++p) {
             for (int q = p + 1; q < n; ++q) {
                 float* xp = &AT(X, 0, p, ldx);
@@ -373,6 +392,9 @@ int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int
                 float az = fabsf(zeta);
                 float t = (az > 1e18f) ? 1.0f / (2.0f * az) : 1.0f / (az + sqrtf(1.0f + az * az));
                 if (zeta < 0.0f) t = -t;
+                const double cs = (double)(fabsf(gamma) / (sqrtf(alpha) * sqrtf(beta)));
+                if (cs > cos_max) cos_max = cs;
+                if (fabsf(t) > tan_max) tan_max = fabsf(t);
                 float c = 1.0f / sqrtf(1.0f + t * t);
                 float s = c * t;
                 for (int i = 0; i < m; ++i) {
@@ -384,6 +406,8 @@ int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int
                 converged = 0;
             }
         }
+        if (!converged && stop == 0 && sweep > 0 && negligible_sweep(n, (double)tol, cos_max, tan_max))
+            converged = 1;
         ++sweep;
     }
     if (sweeps) *sweeps = sweep;
@@ -519,7 +543,7 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
         orc_real* tau2 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
         if (!Xl || !B || !tau2) { free(Xl); free(B); free(tau2); s.status = -9; goto done; }
         for (size_t i = 0; i < nn; ++i) Xl[i] = (float)X[i];
-        orc_jacobi_f32(n, n, Xl, n, (float)(RSQRT((orc_real)n) * U_LOW), p.maxsweep, &s.sweeps_low,
+        orc_jacobi_f32(n, n, Xl, n, (float)(RSQRT((orc_real)n) * U_LOW), p.maxsweep, p.stop, &s.sweeps_low,
                        &s.rot_low);
         /* U_low = normalized columns sorted by descending norm (Alg. 1 final loop and
          * sort), promoted to binary64. The sort matters for the switch: the QR of
@@ -573,7 +597,7 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
     /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated. */
     {
         orc_real tol = (p.tol > 0.0) ? p.tol : RSQRT((orc_real)n) * U_WORK;
-        int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, &s.sweeps_work, &s.rot_work);
+        int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, p.stop, &s.sweeps_work, &s.rot_work);
         if (rc != 0) s.status = 1;
     }
 

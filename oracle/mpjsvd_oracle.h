@@ -45,6 +45,10 @@ typedef struct {
     int qrcp;              /* the RRQR of the preconditioning: 0 -> Businger-Golub in working
                               precision (orc_geqp3), 1 -> the mixed-precision RRQR of Alg. 5
                               (orc_geqp3_mixed) */
+    int stop;              /* when Alg. 1 stops: 0 -> after a sweep without rotations, or after
+                              a sweep (not the first) whose rotations were all negligible, as
+                              the paper's experiments run it (LAPACK's xGESVJ, Section 7.1);
+                              1 -> only after a sweep without rotations (Alg. 1 as printed) */
 } orc_params;
 
 /* What the driver did (per call). */
@@ -98,10 +102,10 @@ void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
  * is also applied to the columns of V (nv x n). Returns 0 if converged, 1 if maxsweep
  * sweeps ran without converging. */
 int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
-               int maxsweep, int* sweeps, long long* rotations);
+               int maxsweep, int stop, int* sweeps, long long* rotations);
 
 /* Alg. 1 in binary32, no V (Alg. 4: "without generating V explicitly"). */
-int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int* sweeps,
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int stop, int* sweeps,
                    long long* rotations);
 
 /* Jacobi rotation for one column pair (Section 2.1): given alpha = |x_p|^2,

@@ -66,6 +66,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->qr_first = 0;
     p->timing = 0;
     p->qrcp = MPJSVD_QRCP_MIXED;
+    p->stop = MPJSVD_STOP_XGESVJ;
     return 0;
 }
 
@@ -76,6 +77,7 @@ static int check_params(const mpjsvd_params* p)
     if (p->mode < 0 || p->mode > 2) return 1;
     if (p->precond < 0 || p->precond > 1) return 1;
     if (p->qrcp < 0 || p->qrcp > 1) return 1;
+    if (p->stop < 0 || p->stop > 1) return 1;
     if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
     return 0;
 }

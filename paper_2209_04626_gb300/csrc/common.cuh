@@ -43,6 +43,8 @@ struct DevState {
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
     unsigned long long amax_bits;          // Alg. 5: max |a_ij| (bits of a non-negative double)
     unsigned long long cand_rec[512];      // Alg. 5: per-CTA step records (tag, column, norm) x parity
+    unsigned mx_cos[2][64];                // binary32 bits: largest cosine among the rotated pairs, [phase][sweep]
+    unsigned mx_tan[2][64];                // binary32 bits: largest |tan| of the rotations, [phase][sweep]
 };
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative

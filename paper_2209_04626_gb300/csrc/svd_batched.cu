@@ -343,6 +343,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         int nb = (n + kBatchWLow - 1) / kBatchWLow;
         D.k = max(2, nb + (nb & 1));
         D.maxsweep = min(P.maxsweep, 64);
+        D.stop = P.stop;
         D.tol = sqrt((double)n) * 5.9604644775390625e-08;
         float* dscf = (float*)(slot + L.dsc);
         D.dsc = dscf;
@@ -352,9 +353,11 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         __syncthreads();
         bool conv = false;
         if (n <= nthr)
-            jacobi_sweeps<float, false, kBatchWLow, 1>(g1, D, Xl, nullptr, st->rot_sweep[0], sm_low, &conv);
+            jacobi_sweeps<float, false, kBatchWLow, 1>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm_low,
+                                                          &conv);
         else
-            jacobi_sweeps<float, false, kBatchWLow, 2>(g1, D, Xl, nullptr, st->rot_sweep[0], sm_low, &conv);
+            jacobi_sweeps<float, false, kBatchWLow, 2>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm_low,
+                                                          &conv);
         fold_scales_cols<float>(g1, n, n, Xl, n, 0, nullptr, n, dscf);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();
@@ -399,6 +402,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         int nb = (n + kBatchWWork - 1) / kBatchWWork;
         D.k = max(2, nb + (nb & 1));
         D.maxsweep = min(P.maxsweep, 64);
+        D.stop = P.stop;
         D.tol = (B.tol > 0.0) ? B.tol : sqrt((double)n) * 1.1102230246251565e-16;
         double* dscd = (double*)(slot + L.dsc);
         D.dsc = dscd;
@@ -408,9 +412,11 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         __syncthreads();
         bool conv = false;
         if (n <= nthr)
-            jacobi_sweeps<double, true, kBatchWWork, 1>(g1, D, Y, Vacc, st->rot_sweep[1], sm_work, &conv);
+            jacobi_sweeps<double, true, kBatchWWork, 1>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm_work,
+                                                            &conv);
         else
-            jacobi_sweeps<double, true, kBatchWWork, 2>(g1, D, Y, Vacc, st->rot_sweep[1], sm_work, &conv);
+            jacobi_sweeps<double, true, kBatchWWork, 2>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm_work,
+                                                            &conv);
         fold_scales_cols<double>(g1, n, n, Y, n, n, Vacc, n, dscd);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();

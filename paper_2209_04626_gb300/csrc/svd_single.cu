@@ -734,6 +734,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         SweepDims Dl;
         Dl.n = n; Dl.mX = n; Dl.ldX = n; Dl.nV = 0; Dl.ldV = n; Dl.w = w_low;
         Dl.k = sweep_blocks(n, w_low); Dl.maxsweep = std::min(P.maxsweep, 64); Dl.tol = tol_low;
+        Dl.stop = P.stop;
         Dl.dsc = dsc; Dl.alph = alph; Dl.ver = ver;
         if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
         k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
@@ -773,6 +774,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     SweepDims Dw;
     Dw.n = n; Dw.mX = n; Dw.ldX = n; Dw.nV = n; Dw.ldV = n; Dw.w = w_work;
     Dw.k = sweep_blocks(n, w_work); Dw.maxsweep = std::min(P.maxsweep, 64); Dw.tol = tol_work;
+    Dw.stop = P.stop;
     Dw.dsc = dsc; Dw.alph = alph; Dw.ver = ver;
     if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
     record(h, 5);

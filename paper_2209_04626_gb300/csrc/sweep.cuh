@@ -180,6 +180,31 @@ __device__ __forceinline__ bool above_tol<float>(float gamma, float al, float be
     return fabsf(gamma) > tol * (sqrtf(al) * sqrtf(be));
 }
 
+// Cosine |gamma| / (|x_a| |x_b|) of a rotated pair as binary32, for the stopping rule. binary64:
+// from the significands and exponents of gamma, alpha, beta (integer arithmetic and binary32
+// only, nothing on the FP64 pipe); 0 when it is below 2^-63, 1 for non-normal norms (a
+// conservative value: it never ends the iteration early).
+__device__ __forceinline__ float pair_cos(double gamma, double al, double be)
+{
+    const long long ig = __double_as_longlong(gamma) & 0x7fffffffffffffffll;
+    const long long ia = __double_as_longlong(al), ib = __double_as_longlong(be);
+    const int eg = (int)(ig >> 52), ea = (int)((ia >> 52) & 0x7ff), eb = (int)((ib >> 52) & 0x7ff);
+    if (eg == 0) return 0.0f;
+    if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff || eg == 0x7ff) return 1.0f;
+    const float mg = __int_as_float(0x3f800000 | (int)((ig >> 29) & 0x7fffff));  // [1, 2)
+    const float ma = __int_as_float(0x3f800000 | (int)((ia >> 29) & 0x7fffff));
+    const float mb = __int_as_float(0x3f800000 | (int)((ib >> 29) & 0x7fffff));
+    const int k2 = 2 * eg - ea - eb;  // cos^2 = mg^2 / (ma mb) * 2^k2
+    if (k2 < -126) return 0.0f;
+    if (k2 > 126) return 1.0f;
+    const float c2 = (mg * mg) / (ma * mb) * __int_as_float((k2 + 127) << 23);
+    return sqrtf(c2);
+}
+__device__ __forceinline__ float pair_cos(float gamma, float al, float be)
+{
+    return fabsf(gamma) / (sqrtf(al) * sqrtf(be));
+}
+
 // Sum of n >= 1 values with a dependency depth of about log2(4) + n / 4 instead of n.
 template <typename T>
 __device__ __forceinline__ T short_sum(const T* v, int n)
@@ -220,6 +245,7 @@ struct SweepDims {
     int w;       // block width (== W of the kernel)
     int k;       // number of blocks (even)
     int maxsweep;
+    int stop;    // MPJSVD_STOP_*: also stop after a negligible sweep (0) or not (1)
     double tol;  // rotation threshold
     void* dsc;   // T[n]: column scales, 1 at the start of the stage
     void* alph;  // T[n]: tracked squared norms (true scale)
@@ -241,6 +267,7 @@ struct VisitShared {
     int gidx[2 * W];
     unsigned act[2 * W];        // active-pair mask per inner round
     int flags[4];               // [0] rotations, [1] norms need recomputing
+    unsigned mxc, mxt;          // binary32 bits: largest cosine and |tan| rotated in the visit
 };
 
 // Pair p of an inner round. Cross rounds: (p, W + (p + q) % W). Intra rounds (W even,
@@ -312,6 +339,7 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
         const int p = tid;
         const int a = pair_a<W>(intra, q, p), b = pair_b<W>(intra, q, p);
         unsigned act = 0;
+        float cs = 0.0f, ta = 0.0f;  // cosine and |tan| of this pair's rotation (stopping rule)
         if (sm.gidx[a] >= 0 && sm.gidx[b] >= 0) {
             const T gh = short_sum(sm.part[p], nw);
             const T da = sm.d[a], db = sm.d[b];
@@ -321,6 +349,8 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
             if (above_tol<T>(gamma, al, be, tol, tol2)) {
                 T t, c, ic;  // tangent, cosine and 1 / cosine of the rotation
                 rot_params(al, be, gamma, t, c, ic);
+                cs = pair_cos(gamma, al, be);
+                ta = fabsf((float)t);
                 sm.tab[slot][p] = t * (db * ia);
                 sm.tba[slot][p] = t * (da * ib);
                 sm.d[a] = da * c;
@@ -336,9 +366,13 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
         }
         // combine the W bits of warp 0's lanes
         unsigned m = __reduce_or_sync((1u << W) - 1u, act);
+        const unsigned mc = __reduce_max_sync((1u << W) - 1u, __float_as_uint(cs));
+        const unsigned mt = __reduce_max_sync((1u << W) - 1u, __float_as_uint(ta));
         if (p == 0) {
             sm.act[slot] = m;
             sm.flags[0] += __popc(m);
+            sm.mxc = max(sm.mxc, mc);
+            sm.mxt = max(sm.mxt, mt);
         }
     }
     __syncthreads();
@@ -438,6 +472,8 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
     if (tid == 0) {
         sm.flags[0] = 0;
         sm.flags[1] = 0;
+        sm.mxc = 0u;
+        sm.mxt = 0u;
     }
     __syncthreads();
 
@@ -550,10 +586,23 @@ __device__ int jacobi_visit(const SweepDims& D, T* X, double* V, int bi, int bj,
 // entries) accumulates the rotations of each sweep. D.dsc must hold 1 and D.alph anything
 // (round 0 recomputes it). Returns the number of sweeps run, or -1 if a barrier failed;
 // *converged tells whether the last sweep rotated nothing.
+// The stopping rule of MPJSVD_STOP_XGESVJ after sweep `sweep` (not the first) with rotations:
+// every rotation of the sweep was negligible (largest cosine among the rotated pairs below
+// sqrt(n) tol, and n times it times the largest |tan| below tol). Reads the sweep's maxima
+// after the barrier that ends it, so every CTA takes the same decision.
+__device__ __forceinline__ bool negligible_sweep(const SweepDims& D, const unsigned* mxc, const unsigned* mxt,
+                                                 int sweep)
+{
+    if (D.stop != 0 || sweep == 0) return false;
+    const double cmax = (double)__uint_as_float(__ldcg(mxc + sweep));
+    const double tmax = (double)__uint_as_float(__ldcg(mxt + sweep));
+    return cmax < sqrt((double)D.n) * D.tol && (double)D.n * cmax * tmax < D.tol;
+}
+
 template <typename T, bool WITH_V, int W, int RPT>
 __device__ int jacobi_sweeps(const Group& g, const SweepDims& D, T* X, double* V,
-                             unsigned long long* rot_sweep, VisitShared<T, W>& sm,
-                             bool* converged)
+                             unsigned long long* rot_sweep, unsigned* mxc, unsigned* mxt,
+                             VisitShared<T, W>& sm, bool* converged)
 {
     const int k = D.k;
     int sweep = 0;
@@ -565,13 +614,18 @@ __device__ int jacobi_sweeps(const Group& g, const SweepDims& D, T* X, double* V
                 int bi, bj;
                 rr_pair(k, r, v, bi, bj);
                 if (bi > bj) { int t = bi; bi = bj; bj = t; }
-                local += (unsigned long long)jacobi_visit<T, WITH_V, W, RPT>(D, X, V, bi, bj, r == 0, sm);
+                const int nr = jacobi_visit<T, WITH_V, W, RPT>(D, X, V, bi, bj, r == 0, sm);
+                local += (unsigned long long)nr;
+                if (threadIdx.x == 0 && nr) {
+                    atomicMax(mxc + sweep, sm.mxc);
+                    atomicMax(mxt + sweep, sm.mxt);
+                }
             }
             if (threadIdx.x == 0 && local) atomicAdd(&rot_sweep[sweep], local);
             if (!g.sync()) return -1;
         }
         unsigned long long total = __ldcg(&rot_sweep[sweep]);
-        if (total == 0) {
+        if (total == 0 || negligible_sweep(D, mxc, mxt, sweep)) {
             *converged = true;
             ++sweep;
             break;
@@ -615,8 +669,8 @@ __device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj,
 // smaller numbers, so the smallest unfinished one can always run (all CTAs are resident).
 template <typename T, bool WITH_V, int W, int RPT>
 __device__ int jacobi_sweeps_flow(const Group& g, const SweepDims& D, T* X, double* V,
-                                  unsigned long long* rot_sweep, unsigned* ver,
-                                  VisitShared<T, W>& sm, bool* converged)
+                                  unsigned long long* rot_sweep, unsigned* mxc, unsigned* mxt,
+                                  unsigned* ver, VisitShared<T, W>& sm, bool* converged)
 {
     const int k = D.k, half = k / 2, rounds = k - 1;
     const long long per_sweep = (long long)rounds * half;
@@ -634,7 +688,11 @@ __device__ int jacobi_sweeps_flow(const Group& g, const SweepDims& D, T* X, doub
             // jacobi_visit_x ends with a CTA barrier: every store of X precedes the release,
             // so the next round's visits of bi and bj can start while this CTA updates V
             if (threadIdx.x == 0) {
-                if (nrot) atomicAdd(&rot_sweep[sweep], (unsigned long long)nrot);
+                if (nrot) {
+                    atomicAdd(&rot_sweep[sweep], (unsigned long long)nrot);
+                    atomicMax(mxc + sweep, sm.mxc);
+                    atomicMax(mxt + sweep, sm.mxt);
+                }
                 __threadfence();
                 st_release_u32(ver + bi, R + 1);
                 st_release_u32(ver + bj, R + 1);
@@ -652,7 +710,7 @@ __device__ int jacobi_sweeps_flow(const Group& g, const SweepDims& D, T* X, doub
             }
         }
         if (!g.sync()) return -1;
-        if (__ldcg(&rot_sweep[sweep]) == 0) {
+        if (__ldcg(&rot_sweep[sweep]) == 0 || negligible_sweep(D, mxc, mxt, sweep)) {
             *converged = true;
             ++sweep;
             break;

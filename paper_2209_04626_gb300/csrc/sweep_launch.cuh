@@ -31,7 +31,8 @@ __global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, 
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 2 * D.k; b += gridDim.x * blockDim.x) D.ver[b] = 0u;
     if (!g.sync()) return;
     bool conv = false;
-    int sweeps = jacobi_sweeps_flow<T, WITH_V, W, RPT>(g, D, X, V, st->rot_sweep[phase], D.ver, sm, &conv);
+    int sweeps = jacobi_sweeps_flow<T, WITH_V, W, RPT>(g, D, X, V, st->rot_sweep[phase], st->mx_cos[phase],
+                                                       st->mx_tan[phase], D.ver, sm, &conv);
     if (sweeps < 0) return;
     fold_scales_cols<T>(g, D.mX, D.n, X, D.ldX, WITH_V ? D.nV : 0, WITH_V ? V : nullptr, D.ldV, dsc);
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmpjsvd.so")
 MODE = {"auto": 0, "mixed": 1, "plain": 2}
 PRECOND = {"rt": 0, "r": 1}
 QRCP = {"mixed": 0, "f64": 1}
+STOP = {"xgesvj": 0, "alg1": 1}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -33,7 +34,7 @@ class Params(ctypes.Structure):
                 ("tol_cond_coef", ctypes.c_double), ("trailing_frac", ctypes.c_double),
                 ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
-                ("qrcp", ctypes.c_int)]
+                ("qrcp", ctypes.c_int), ("stop", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -104,6 +105,8 @@ def mpjsvd_default_params(**overrides):
             v = PRECOND[v]
         if k == "qrcp" and isinstance(v, str):
             v = QRCP[v]
+        if k == "stop" and isinstance(v, str):
+            v = STOP[v]
         setattr(p, k, v)
     return p
 
@@ -210,6 +213,8 @@ class Handle:
                 v = PRECOND[v]
             if k == "qrcp" and isinstance(v, str):
                 v = QRCP[v]
+            if k == "stop" and isinstance(v, str):
+                v = STOP[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 

@@ -292,6 +292,52 @@ def test_jacobi_f64_and_f32_converge_to_svd():
     assert np.abs(Xn.T @ Xn - np.eye(n)).max() < 1e-5
 
 
+def _max_cos(X):
+    Xn = X / np.linalg.norm(X, axis=0)
+    G = np.abs(Xn.T @ Xn)
+    np.fill_diagonal(G, 0.0)
+    return G.max()
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_negligible_sweep_stop(seed):
+    """The stopping rule of the paper's experiments (stop = 0): it ends no later than Alg. 1 as
+    printed (stop = 1), gives the same singular values, and at exit no column pair is more
+    than sqrt(n) tol from orthogonal (the rule's premise: the last sweep rotated only pairs
+    below sqrt(n) tol, by angles too small to move the others)."""
+    rng = np.random.default_rng(seed)
+    m, n = 80, 48
+    A = inputs.known_sigma(rng, m, n, np.logspace(0, -6, n))
+    tol = np.sqrt(m) * U64
+    X0, V0, sw0, rot0, rc0 = oracle.jacobi(A, np.eye(n), stop=0)
+    X1, V1, sw1, rot1, rc1 = oracle.jacobi(A, np.eye(n), stop=1)
+    assert rc0 == 0 and rc1 == 0
+    assert sw0 <= sw1 and rot0 <= rot1
+    s0 = np.sort(np.linalg.norm(X0, axis=0))[::-1]
+    s1 = np.sort(np.linalg.norm(X1, axis=0))[::-1]
+    assert np.max(np.abs(s0 - s1) / s1) < 1e-13
+    assert _max_cos(X0) <= 2 * np.sqrt(n) * tol
+    assert np.abs(V0.T @ V0 - np.eye(n)).max() < 64 * n * U64
+    # binary32 stage, same rule
+    Xf0, swf0, _, rcf0 = oracle.jacobi_f32(A, stop=0)
+    Xf1, swf1, _, rcf1 = oracle.jacobi_f32(A, stop=1)
+    assert rcf0 == 0 and rcf1 == 0 and swf0 <= swf1
+    assert _max_cos(Xf0.astype(np.float64)) <= 2 * np.sqrt(n) * np.sqrt(m) * 2.0 ** -24
+
+
+def test_negligible_sweep_needs_two_sweeps():
+    """A sweep that rotates nothing ends Alg. 1 under both rules, and the first sweep never
+    ends it early: a pair that starts above the threshold takes two sweeps either way."""
+    n = 6
+    X = np.eye(n)
+    X[0, 1] = 1e-10  # columns 0 and 1 at cosine 1e-10, far above tol = sqrt(6) u
+    _, _, sw0, rot0, _ = oracle.jacobi(X, stop=0)
+    _, _, sw1, rot1, _ = oracle.jacobi(X, stop=1)
+    assert (sw0, rot0) == (2, 1) and (sw1, rot1) == (2, 1)
+    _, _, sw, rot, _ = oracle.jacobi(np.eye(n), stop=0)
+    assert (sw, rot) == (1, 0)
+
+
 def test_mixed_and_plain_agree():
     rng = np.random.default_rng(15)
     A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
