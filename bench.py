@@ -43,6 +43,10 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=3)
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--large", action="store_true",
+                   help="the 8192 x 8192 comparison instead: one mixed and one plain call, "
+                        "phase times, sweeps and accuracy (one JSON line; not the headline)")
+    p.add_argument("--large-n", type=int, default=8192)
     return p.parse_args()
 
 
@@ -434,10 +438,57 @@ def ours(args):
     return 0
 
 
+def large(args):
+    """8192 x 8192 A = B D (B: sigma log-spaced 1 .. 1e-2, D = diag(10^U(-10, 0)), seed 4):
+    the full mixed pipeline beside plain binary64 Jacobi, one call each through the public API,
+    with per-phase times, sweep and rotation counts and the accuracy invariants."""
+    import torch
+    from paper_2209_04626_gb300 import inputs, mpjsvd
+    n = args.large_n
+    A = mpjsvd.colmajor(torch.from_numpy(inputs.large_8192(n=n)), torch.device("cuda"))
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    res, S_ref = {}, None
+    for mode in ("mixed", "plain"):
+        h = mpjsvd.Handle(mode=mode, timing=1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        U, S, V = h.svd(A)
+        e1.record()
+        torch.cuda.synchronize()
+        st = h.stats()
+        I = torch.eye(n, dtype=torch.float64, device="cuda")
+        d = {"s": e0.elapsed_time(e1) / 1e3, "status": st["status"], "qrcp": st["qrcp"],
+             "sweeps_low": st["sweeps_low"], "sweeps_work": st["sweeps_work"],
+             "rot_low": st["rot_low"], "rot_work": st["rot_work"],
+             "phases_ms": {k: round(st[k], 1) for k in ("ms_qr", "ms_branch", "ms_low", "ms_switch",
+                                                        "ms_work", "ms_final")},
+             "backward_fro": (torch.linalg.matrix_norm((U * S) @ V.T - A) /
+                              torch.linalg.matrix_norm(A)).item(),
+             "orth_U_max": (U.T @ U - I).abs().max().item(),
+             "orth_V_max": (V.T @ V - I).abs().max().item(),
+             "bound_orth": 64 * n * 2.0 ** -53}
+        if S_ref is None:
+            S_ref = S.clone()
+        else:
+            d["max_rel_sigma_vs_mixed"] = ((S - S_ref).abs() / S_ref).max().item()
+        res[mode] = d
+        del U, S, V, h, I
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    print(json.dumps({"workload": "large_%d: A = B D, B sigma logspace(0,-2), D = diag(10^U(-10,0)), "
+                                  "seed 4" % n, "unit": "s per SVD",
+                      "mixed_over_plain": res["plain"]["s"] / res["mixed"]["s"], "clocks": clk, **res}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.large:
+        return large(args)
     return ours(args)
 
 
