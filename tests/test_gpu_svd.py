@@ -139,3 +139,26 @@ def test_repeated_calls_same_handle_deterministic():
     U2, S2, V2 = [t.cpu().numpy() for t in h.svd(Ad)]
     assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)
     h.close()
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_stop_rules(mode):
+    """Both stopping rules of Alg. 1 (R22): the default (xGESVJ's, with which the paper's
+    experiments run) never takes more sweeps than Alg. 1 as printed, both meet every bar, and
+    their singular values agree to the working precision; each matches the oracle run with the
+    same rule."""
+    A, _ = inputs.plain_256x128()
+    out = {}
+    for stop in ("xgesvj", "alg1"):
+        U, S, V, st = gpu_svd(A, mode, stop=stop)
+        assert st["status"] == 0, st
+        check_factorization(A, U, S, V)
+        check_sign_rule(V)
+        _, So, _, _ = oracle.svd(A, mode=mode, stop=0 if stop == "xgesvj" else 1)
+        sigma_gate(A, S, So)
+        out[stop] = (S, st)
+    (S0, st0), (S1, st1) = out["xgesvj"], out["alg1"]
+    assert st0["sweeps_work"] <= st1["sweeps_work"]
+    if mode == "mixed":
+        assert st0["sweeps_low"] <= st1["sweeps_low"]
+    assert np.max(np.abs(S0 - S1) / S1) < 1e-13
