@@ -162,3 +162,20 @@ def test_stop_rules(mode):
     if mode == "mixed":
         assert st0["sweeps_low"] <= st1["sweeps_low"]
     assert np.max(np.abs(S0 - S1) / S1) < 1e-13
+
+
+def test_binary32_stage_resolves_small_columns():
+    """Columns down to 3e-13 of the largest (A = B D, D = 10^U(-12, 0)): the binary32 stage
+    must rotate pairs of small columns too (the test |gamma| > tol |x_p| |x_q| with square roots;
+    compared as squares, alpha beta underflows binary32 and those pairs stay unresolved, which
+    leaves their work to the binary64 refinement). The refinement then needs no more sweeps
+    than the oracle's plus one, and the result meets every bar."""
+    rng = np.random.default_rng(21)
+    B = inputs.known_sigma(rng, 256, 128, np.logspace(0, -2, 128))
+    A = B * 10.0 ** rng.uniform(-12, 0, 128)
+    U, S, V, st = gpu_svd(A, "mixed")
+    _, So, _, sto = oracle.svd(A, mode="mixed")
+    assert st["status"] == 0 and st["branch"] == 0, st
+    check_factorization(A, U, S, V)
+    sigma_gate(A, S, So)
+    assert st["sweeps_work"] <= sto["sweeps_work"] + 1, (st["sweeps_work"], sto["sweeps_work"])
