@@ -120,6 +120,10 @@ int mpjsvd_default_params(mpjsvd_params* p);
  * mpjsvd_set_stream(). */
 int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream);
 
+/* Switch the handle's stream. The new stream is made to wait (on the device, through an
+ * event; the host does not block) for the work already queued on the previous one, since the
+ * workspace is shared by all calls of the handle. Passing the current stream is a no-op.
+ * Returns 0, -1 if h is NULL, MPJSVD_ERR_CUDA if the ordering could not be set up. */
 int mpjsvd_set_stream(mpjsvd_handle h, void* cuda_stream);
 int mpjsvd_set_params(mpjsvd_handle h, const mpjsvd_params* p);
 

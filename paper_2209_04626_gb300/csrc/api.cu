@@ -105,8 +105,11 @@ int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream)
     e = cudaMalloc(&c->dstate, sizeof(DevState));
     if (e != cudaSuccess) { delete c; set_last_error("state cudaMalloc", e); return MPJSVD_ERR_NOMEM; }
     c->have_events = true;
-    for (int i = 0; i < 8; ++i)
-        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
+    for (int i = 0; i < 8 && c->have_events; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(c->ev[k]);
+            c->have_events = false;
+        }
     // look-ahead streams: when both CTAs of the critical chain and of a wide update are
     // waiting for an SM, the critical chain's go first
     int prio_lo = 0, prio_hi = 0;
@@ -131,7 +134,17 @@ int mpjsvd_create(mpjsvd_handle* h, const mpjsvd_params* p, void* cuda_stream)
 int mpjsvd_set_stream(mpjsvd_handle h, void* cuda_stream)
 {
     if (!h) return -1;
-    h->stream = (cudaStream_t)cuda_stream;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (s == h->stream) return 0;
+    // the workspace is shared by all calls of the handle: the new stream waits (on the device)
+    // for the work already queued on the previous one before a call reuses it
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+    cudaEventDestroy(ev);  // released once the wait has been satisfied
+    if (e != cudaSuccess) return cuda_fail("set_stream: order after the previous stream", e);
+    h->stream = s;
     return 0;
 }
 
