@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 MODE = {"auto": 0, "mixed": 1, "plain": 2}
-PRECOND = {"rt": 0, "r": 1}
+PRECOND = {"rt": 0, "r": 1, "l": 2, "auto": 3}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain"}
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -40,7 +40,7 @@ class _Variant:
             _fields_ = [("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
                         ("sweeps_work", ctypes.c_int), ("rot_low", ctypes.c_longlong),
                         ("rot_work", ctypes.c_longlong), ("cond_r", creal), ("orth", creal),
-                        ("switch_off", creal), ("status", ctypes.c_int)]
+                        ("switch_off", creal), ("status", ctypes.c_int), ("precond", ctypes.c_int)]
 
             def as_dict(self):
                 d = {name: getattr(self, name) for name, _ in self._fields_}

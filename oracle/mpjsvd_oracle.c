@@ -467,6 +467,8 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
     orc_real* Ux = (orc_real*)calloc((size_t)m * (size_t)n, sizeof(orc_real));
     int* order = (int*)malloc(sizeof(int) * (size_t)n);
     orc_real* sig = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
+    orc_real* Lq = NULL;   /* R^T = Q' R' (geqrf layout) when X = L: L = R'^T, Q2 = Q'^T */
+    orc_real* tauq = NULL;
     if (!W0 || !tau0 || !R || !tau1 || !jpvt || !X || !Y || !Vacc || !Ux || !order || !sig) {
         s.status = -9;
         goto done;
@@ -483,14 +485,40 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) AT(R, i, j, n) = AT(W0, i, j, m);
     }
-    /* QR preconditioning: A1 P = Q1 R; X = R^T (default) or X = R (Q2 = I). */
+    /* QR preconditioning: A1 P = Q1 R; X = R^T (default), X = R (Q2 = I), or X = L from
+     * R = L Q2 (Alg. 2). */
     if (p.qrcp == 1) orc_geqp3_mixed(n, n, R, n, jpvt, tau1);
     else orc_geqp3(n, n, R, n, jpvt, tau1);
-    for (int j = 0; j < n; ++j)
-        for (int i = 0; i <= j; ++i) {
-            if (p.precond == 1) AT(X, i, j, n) = AT(R, i, j, n);
-            else AT(X, j, i, n) = AT(R, i, j, n);
+    int pc = p.precond;
+    if (pc == 3) {
+        /* Alg. 2's test "R is almost diagonal", read as: every column of R is diagonally
+         * dominant, |r_jj| >= sum_{i<j} |r_ij| (the paper's "close to diagonally dominant") */
+        int dominant = 1;
+        for (int j = 0; j < n && dominant; ++j) {
+            orc_real off = 0.0;
+            for (int i = 0; i < j; ++i) off += RFABS(AT(R, i, j, n));
+            if (off > RFABS(AT(R, j, j, n))) dominant = 0;
         }
+        pc = dominant ? 1 : 2;
+    }
+    s.precond = (pc == 1) ? 1 : (pc == 2 ? 2 : 0);
+    if (pc == 2) {
+        /* LQ of R as the QR of R^T: R^T = Q' R', so R = R'^T Q'^T, L = R'^T, Q2 = Q'^T */
+        Lq = (orc_real*)calloc(nn, sizeof(orc_real));
+        tauq = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
+        if (!Lq || !tauq) { s.status = -9; goto done; }
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i <= j; ++i) AT(Lq, j, i, n) = AT(R, i, j, n);
+        orc_geqrf(n, n, Lq, n, tauq);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i <= j; ++i) AT(X, j, i, n) = AT(Lq, i, j, n);
+    } else {
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i <= j; ++i) {
+                if (pc == 1) AT(X, i, j, n) = AT(R, i, j, n);
+                else AT(X, j, i, n) = AT(R, i, j, n);
+            }
+    }
 
     /* Special cases of Section 3.5. */
     {
@@ -613,14 +641,16 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
         order[b + 1] = oj;
     }
     /* X = U_X Sigma V_acc^T. For X = R: U_R = U_X, V_R = V_acc. For X = R^T the roles
-     * exchange: R = V_acc Sigma U_X^T, so U_R = V_acc and V_R = U_X. */
+     * exchange: R = V_acc Sigma U_X^T, so U_R = V_acc and V_R = U_X. For X = L = R Q':
+     * R = U_X Sigma (Q' V_acc)^T, so U_R = U_X and V_R = Q' V_acc. */
+    if (pc == 2) orc_apply_q(0, n, n, n, Lq, n, tauq, Vacc, n);
     for (int k = 0; k < n; ++k) {
         int j = order[k];
         S[k] = sig[j];
         for (int i = 0; i < n; ++i) {
             orc_real ux = (sig[j] > 0.0) ? AT(Y, i, j, n) / sig[j] : 0.0;
-            orc_real uR = (p.precond == 1) ? ux : AT(Vacc, i, j, n);
-            orc_real vR = (p.precond == 1) ? AT(Vacc, i, j, n) : ux;
+            orc_real uR = (pc == 0) ? AT(Vacc, i, j, n) : ux;
+            orc_real vR = (pc == 0) ? ux : AT(Vacc, i, j, n);
             AT(Ux, i, k, m) = uR;
             /* V = P V_R: row jpvt[i] of V is row i of V_R (Alg. 2, V <- P V_X). */
             AT(V, jpvt[i], k, n) = vR;
@@ -641,7 +671,7 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
 
 done:
     free(W0); free(tau0); free(R); free(tau1); free(jpvt); free(X); free(Y);
-    free(Vacc); free(Ux); free(order); free(sig);
+    free(Vacc); free(Ux); free(order); free(sig); free(Lq); free(tauq);
     if (st) *st = s;
     return s.status;
 }

@@ -41,7 +41,10 @@ typedef struct {
                               2 never run it (plain FP64 preconditioned Jacobi, Alg. 2) */
     int precond;           /* Jacobi input after the QRCP A1 P = Q1 R: 0 -> X = R^T (lower
                               triangular; SVD of R with the roles of U and V exchanged),
-                              1 -> X = R (Alg. 4 with Q2 = I) */
+                              1 -> X = R (Alg. 4 with Q2 = I), 2 -> X = L from the LQ
+                              factorization R = L Q2 (Alg. 2's else branch), 3 -> Alg. 2's
+                              choice: X = R when every column of R is diagonally dominant,
+                              else X = L */
     int qrcp;              /* the RRQR of the preconditioning: 0 -> Businger-Golub in working
                               precision (orc_geqp3), 1 -> the mixed-precision RRQR of Alg. 5
                               (orc_geqp3_mixed) */
@@ -64,6 +67,7 @@ typedef struct {
     orc_real orth;           /* max |Xt^T Xt - I| of the column-scaled low(X), FP32 */
     orc_real switch_off;     /* max_{i!=j} |y_i^T y_j| / (|y_i||y_j|) right after the switch */
     int status;            /* 0 ok, 1 FP64 sweeps hit maxsweep, 2 non-finite input, <0 bad argument */
+    int precond;           /* the Jacobi input that ran: 0 R^T, 1 R, 2 L */
 } orc_stats;
 
 void orc_default_params(orc_params* p);

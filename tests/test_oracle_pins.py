@@ -338,6 +338,41 @@ def test_negligible_sweep_needs_two_sweeps():
     assert (sw, rot) == (1, 0)
 
 
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_lq_preconditioning(mode):
+    """Alg. 2's else branch, X = L from R = L Q2: the same SVD as X = R^T (the singular values
+    of R and of L = R Q2^T are the same; V = P Q2^T V_X), orthogonal factors, A = U S V^T."""
+    rng = np.random.default_rng(41)
+    A = inputs.known_sigma(rng, 70, 48, np.logspace(0, -4, 48))
+    Ur, Sr, Vr, str_ = oracle.svd(A, mode=mode, precond="rt")
+    Ul, Sl, Vl, stl = oracle.svd(A, mode=mode, precond="l")
+    assert str_["precond"] == 0 and stl["precond"] == 2 and stl["status"] == 0
+    assert np.max(np.abs(Sl - Sr) / Sr) < 1e-13
+    n = A.shape[1]
+    assert np.abs(Ul.T @ Ul - np.eye(n)).max() < 64 * n * U64
+    assert np.abs(Vl.T @ Vl - np.eye(n)).max() < 64 * n * U64
+    assert np.linalg.norm(A - (Ul * Sl) @ Vl.T) / np.linalg.norm(A) < 1e-14
+    # well separated singular values: the vectors agree up to sign (sign rule: same choice)
+    assert np.abs(Vl - Vr).max() < 1e-10 and np.abs(Ul - Ur).max() < 1e-10
+
+
+def test_lq_choice_diagonal_dominance():
+    """Alg. 2's choice: X = R when every column of R is diagonally dominant, else X = L."""
+    rng = np.random.default_rng(42)
+    n = 32
+    # nearly orthogonal columns of graded norms: R = diag + O(1e-3) per entry, dominant
+    A = (np.eye(n) + 1e-3 * rng.standard_normal((n, n))) @ np.diag(np.logspace(0, -3, n))
+    _, S1, _, st1 = oracle.svd(A, mode="plain", precond="auto")
+    assert st1["precond"] == 1
+    # dense with a flat spectrum: the columns of R are not dominant
+    B = inputs.known_sigma(rng, n, n, np.linspace(1.0, 0.5, n))
+    _, S2, _, st2 = oracle.svd(B, mode="plain", precond="auto")
+    assert st2["precond"] == 2
+    for M, S in ((A, S1), (B, S2)):
+        s_ref = np.linalg.svd(M, compute_uv=False)
+        assert np.max(np.abs(S - s_ref) / s_ref) < 1e-13
+
+
 def test_mixed_and_plain_agree():
     rng = np.random.default_rng(15)
     A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
