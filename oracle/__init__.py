@@ -34,7 +34,7 @@ class _Variant:
             _fields_ = [("tol_alg", creal), ("tol_orth", creal), ("tol_cond_coef", creal),
                         ("trailing_frac", creal), ("tol", creal), ("maxsweep", ctypes.c_int),
                         ("mode", ctypes.c_int), ("precond", ctypes.c_int), ("qrcp", ctypes.c_int),
-                        ("stop", ctypes.c_int)]
+                        ("switch_method", ctypes.c_int), ("stop", ctypes.c_int)]
 
         class Stats(ctypes.Structure):
             _fields_ = [("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
@@ -62,8 +62,9 @@ class _Variant:
         L.orc_jacobi.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, ctypes.c_int,
                                  ctypes.c_int, creal, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.POINTER(ctypes.c_longlong)]
-        L.orc_jacobi_f32.argtypes = [ctypes.c_int, ctypes.c_int, _fp, ctypes.c_int, ctypes.c_float,
-                                     ctypes.c_int, ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_jacobi_f32.argtypes = [ctypes.c_int, ctypes.c_int, _fp, ctypes.c_int, _fp, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _ip,
+                                     ctypes.POINTER(ctypes.c_longlong)]
         L.orc_rot_tangent.argtypes = [creal, creal, creal]
         L.orc_rot_tangent.restype = creal
         L.orc_svd.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, rp, rp,
@@ -209,8 +210,8 @@ def jacobi_f32(X, tol=None, maxsweep=30, stop=0):
     tol = np.sqrt(m) * 2.0 ** -24 if tol is None else tol
     sw = ctypes.c_int()
     rot = ctypes.c_longlong()
-    rc = L.orc_jacobi_f32(m, n, X.ctypes.data_as(_fp), m, tol, maxsweep, stop, ctypes.byref(sw),
-                          ctypes.byref(rot))
+    rc = L.orc_jacobi_f32(m, n, X.ctypes.data_as(_fp), m, None, 1, 0, tol, maxsweep, stop,
+                          ctypes.byref(sw), ctypes.byref(rot))
     return X, sw.value, rot.value, rc
 
 

@@ -41,6 +41,7 @@ void orc_default_params(orc_params* p)
     p->mode = 0;
     p->precond = 0;
     p->qrcp = 0;
+    p->switch_method = 0;
     p->stop = 0;
 }
 
@@ -369,8 +370,8 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
 
 /* Alg. 1 in binary32 without V (the lower-precision stage of Alg. 4). Same steps and
  * stopping rules as orc_jacobi; every operation rounds to binary32. */
-int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int stop, int* sweeps,
-                   long long* rotations)
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float* V, int ldv, int nv, float tol, int maxsweep,
+                   int stop, int* sweeps, long long* rotations)
 {
     long long rot = 0;
     int sweep = 0, converged = 0;
@@ -401,6 +402,15 @@ int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int
                     float a = xp[i], b = xq[i];
                     xp[i] = c * a - s * b;
                     xq[i] = s * a + c * b;
+                }
+                if (V) {
+                    float* vp = &AT(V, 0, p, ldv);
+                    float* vq = &AT(V, 0, q, ldv);
+                    for (int i = 0; i < nv; ++i) {
+                        float a = vp[i], b = vq[i];
+                        vp[i] = c * a - s * b;
+                        vq[i] = s * a + c * b;
+                    }
                 }
                 ++rot;
                 converged = 0;
@@ -571,8 +581,33 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
         orc_real* tau2 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
         if (!Xl || !B || !tau2) { free(Xl); free(B); free(tau2); s.status = -9; goto done; }
         for (size_t i = 0; i < nn; ++i) Xl[i] = (float)X[i];
-        orc_jacobi_f32(n, n, Xl, n, (float)(RSQRT((orc_real)n) * U_LOW), p.maxsweep, p.stop, &s.sweeps_low,
-                       &s.rot_low);
+        float* Vl = NULL;  /* binary32 V of the low stage, only for the alternative switch */
+        if (p.switch_method == 1) {
+            Vl = (float*)calloc(nn, sizeof(float));
+            if (!Vl) { free(Xl); free(B); free(tau2); s.status = -9; goto done; }
+            for (int j = 0; j < n; ++j) AT(Vl, j, j, n) = 1.0f;
+        }
+        orc_jacobi_f32(n, n, Xl, n, Vl, n, Vl ? n : 0, (float)(RSQRT((orc_real)n) * U_LOW), p.maxsweep,
+                       p.stop, &s.sweeps_low, &s.rot_low);
+        if (Vl) {
+            /* Alternative switch: V_low = Q2 R2 in binary64, Y = X Q2, V_acc = Q2. */
+            for (size_t i = 0; i < nn; ++i) B[i] = (orc_real)Vl[i];
+            free(Vl);
+            orc_geqrf(n, n, B, n, tau2);
+            for (int j = 0; j < n; ++j) AT(Vacc, j, j, n) = 1.0;
+            orc_apply_q(0, n, n, n, B, n, tau2, Vacc, n);
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    orc_real acc = 0.0;
+                    for (int i = 0; i < n; ++i) acc += AT(X, a, i, n) * AT(Vacc, i, b, n);
+                    AT(Y, a, b, n) = acc;
+                }
+            s.switch_off = scaled_offdiag(n, n, Y);
+            free(Xl);
+            free(B);
+            free(tau2);
+            goto refine;
+        }
         /* U_low = normalized columns sorted by descending norm (Alg. 1 final loop and
          * sort), promoted to binary64. The sort matters for the switch: the QR of
          * B = X^T U_low removes from each column its error along the directions of the
@@ -622,6 +657,7 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
         s.switch_off = scaled_offdiag(n, n, Y);
     }
 
+refine:
     /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated. */
     {
         orc_real tol = (p.tol > 0.0) ? p.tol : RSQRT((orc_real)n) * U_WORK;

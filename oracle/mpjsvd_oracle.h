@@ -48,6 +48,10 @@ typedef struct {
     int qrcp;              /* the RRQR of the preconditioning: 0 -> Businger-Golub in working
                               precision (orc_geqp3), 1 -> the mixed-precision RRQR of Alg. 5
                               (orc_geqp3_mixed) */
+    int switch_method;     /* precision switch (Section 3.3 and the section on its efficiency):
+                              0 -> B = X^T U_low, B = Q1 R1, Y = X Q1 (the paper's choice);
+                              1 -> V_low accumulated by the binary32 stage, V_low = Q2 R2,
+                              Y = X Q2 (the alternative it compares against) */
     int stop;              /* when Alg. 1 stops: 0 -> after a sweep without rotations, or after
                               a sweep (not the first) whose rotations were all negligible, as
                               the paper's experiments run it (LAPACK's xGESVJ, Section 7.1);
@@ -108,9 +112,10 @@ void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
 int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
                int maxsweep, int stop, int* sweeps, long long* rotations);
 
-/* Alg. 1 in binary32, no V (Alg. 4: "without generating V explicitly"). */
-int orc_jacobi_f32(int m, int n, float* X, int ldx, float tol, int maxsweep, int stop, int* sweeps,
-                   long long* rotations);
+/* Alg. 1 in binary32 (Alg. 4: "without generating V explicitly"; V (nv x n, binary32) is
+ * accumulated only when not NULL, for the alternative switch). */
+int orc_jacobi_f32(int m, int n, float* X, int ldx, float* V, int ldv, int nv, float tol, int maxsweep,
+                   int stop, int* sweeps, long long* rotations);
 
 /* Jacobi rotation for one column pair (Section 2.1): given alpha = |x_p|^2,
  * beta = |x_q|^2, gamma = x_p^T x_q (gamma != 0), the tangent t of the rotation closest

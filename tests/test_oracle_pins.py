@@ -373,6 +373,24 @@ def test_lq_choice_diagonal_dominance():
         assert np.max(np.abs(S - s_ref) / s_ref) < 1e-13
 
 
+@pytest.mark.parametrize("seed", [0, 51, 52])
+def test_switch_methods(seed):
+    """The two ways to switch precisions compared in the paper's section on the switch's
+    efficiency: Y1 = X Q1 from the QR of B = X^T U_low (the default) has more orthogonal
+    columns than Y2 = X Q2 from the QR of the binary32-accumulated V_low; both refine to
+    the same singular values."""
+    if seed == 0:
+        A, _ = inputs.plain_256x128()
+    else:
+        rng = np.random.default_rng(seed)
+        B = inputs.known_sigma(rng, 120, 80, np.logspace(0, -2, 80))
+        A = B * 10.0 ** rng.uniform(-8, 0, 80)
+    _, S1, _, st1 = oracle.svd(A, mode="mixed", switch_method=0)
+    _, S2, _, st2 = oracle.svd(A, mode="mixed", switch_method=1)
+    assert st1["switch_off"] < st2["switch_off"] < 1e-4
+    assert np.max(np.abs(S1 - S2) / S2) < 1e-13
+
+
 def test_mixed_and_plain_agree():
     rng = np.random.default_rng(15)
     A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
