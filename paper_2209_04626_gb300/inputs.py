@@ -43,7 +43,10 @@ def xlatm1(rng, mode, n, kappa):
     elif mode == 3:
         d = kappa ** (-i / max(n - 1, 1))
     elif mode == 4:
-        d = 1.0 - i / max(n - 1, 1) * (1.0 - 1.0 / kappa)
+        # 1 - t (1 - 1/kappa) with t = (i-1)/(n-1), evaluated as (1 - t) + t / kappa: the same
+        # numbers without the cancellation that turns d(n) = 1/kappa into 0 for kappa > 1e16
+        t = i / max(n - 1, 1)
+        d = (1.0 - t) + t / kappa
     elif mode == 5:
         d = np.exp(rng.uniform(np.log(1.0 / kappa), 0.0, n))
     else:
