@@ -42,6 +42,7 @@ void orc_default_params(orc_params* p)
     p->precond = 0;
     p->qrcp = 0;
     p->switch_method = 0;
+    p->v_by_qr = 0;
     p->stop = 0;
 }
 
@@ -658,11 +659,56 @@ int orc_svd(int m, int n, const orc_real* A, int lda, orc_real* U, orc_real* S, 
     }
 
 refine:
-    /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated. */
+    /* Refinement in working precision (Section 3.4): Alg. 1 on Y with V accumulated, or
+     * (v_by_qr) without V, then V_X from the QR of X^T U_X (U_X sorted by descending norm, as
+     * for the switch) and Alg. 1 with V accumulated from that start on Y = X Q3. */
     {
         orc_real tol = (p.tol > 0.0) ? p.tol : RSQRT((orc_real)n) * U_WORK;
-        int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, p.stop, &s.sweeps_work, &s.rot_work);
-        if (rc != 0) s.status = 1;
+        if (!p.v_by_qr) {
+            int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, p.stop, &s.sweeps_work, &s.rot_work);
+            if (rc != 0) s.status = 1;
+        } else {
+            int rc = orc_jacobi(n, n, Y, n, NULL, 1, 0, tol, p.maxsweep, p.stop, &s.sweeps_work, &s.rot_work);
+            if (rc != 0) s.status = 1;
+            orc_real* B3 = (orc_real*)malloc(sizeof(orc_real) * nn);
+            orc_real* tau3 = (orc_real*)malloc(sizeof(orc_real) * (size_t)n);
+            if (!B3 || !tau3) { free(B3); free(tau3); s.status = -9; goto done; }
+            for (int j = 0; j < n; ++j) {
+                sig[j] = nrm2(n, &AT(Y, 0, j, n));
+                order[j] = j;
+            }
+            for (int a = 1; a < n; ++a) { /* stable insertion sort, descending */
+                int oj = order[a];
+                int b = a - 1;
+                while (b >= 0 && sig[order[b]] < sig[oj]) { order[b + 1] = order[b]; --b; }
+                order[b + 1] = oj;
+            }
+            for (int b = 0; b < n; ++b) { /* B3 = X^T U_X */
+                const int j = order[b];
+                const orc_real inv = (sig[j] > 0.0) ? 1.0 / sig[j] : 0.0;
+                for (int a = 0; a < n; ++a) {
+                    orc_real acc = 0.0;
+                    for (int i = 0; i < n; ++i) acc += AT(X, i, a, n) * AT(Y, i, j, n);
+                    AT(B3, a, b, n) = acc * inv;
+                }
+            }
+            orc_geqrf(n, n, B3, n, tau3);
+            memset(Vacc, 0, sizeof(orc_real) * nn);
+            for (int j = 0; j < n; ++j) AT(Vacc, j, j, n) = 1.0;
+            orc_apply_q(0, n, n, n, B3, n, tau3, Vacc, n); /* Vacc = Q3 */
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    orc_real acc = 0.0;
+                    for (int i = 0; i < n; ++i) acc += AT(X, a, i, n) * AT(Vacc, i, b, n);
+                    AT(Y, a, b, n) = acc;
+                }
+            free(B3);
+            free(tau3);
+            long long rot_v = 0;
+            rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, p.stop, &s.sweeps_v, &rot_v);
+            if (rc != 0) s.status = 1;
+            s.rot_work += rot_v;
+        }
     }
 
     /* Sigma = column norms, U_X = normalized columns, sorted descending (Alg. 1). */

@@ -52,6 +52,9 @@ typedef struct {
                               0 -> B = X^T U_low, B = Q1 R1, Y = X Q1 (the paper's choice);
                               1 -> V_low accumulated by the binary32 stage, V_low = Q2 R2,
                               Y = X Q2 (the alternative it compares against) */
+    int v_by_qr;           /* right singular vectors (Section 3.4): 0 -> accumulated through the
+                              refinement sweeps; 1 -> refinement without V, then V_X from the
+                              QR of X^T U_X and one more Alg. 1 with V from that start */
     int stop;              /* when Alg. 1 stops: 0 -> after a sweep without rotations, or after
                               a sweep (not the first) whose rotations were all negligible, as
                               the paper's experiments run it (LAPACK's xGESVJ, Section 7.1);
@@ -72,6 +75,7 @@ typedef struct {
     orc_real switch_off;     /* max_{i!=j} |y_i^T y_j| / (|y_i||y_j|) right after the switch */
     int status;            /* 0 ok, 1 FP64 sweeps hit maxsweep, 2 non-finite input, <0 bad argument */
     int precond;           /* the Jacobi input that ran: 0 R^T, 1 R, 2 L */
+    int sweeps_v;          /* v_by_qr = 1: sweeps of the final Alg. 1 with V */
 } orc_stats;
 
 void orc_default_params(orc_params* p);

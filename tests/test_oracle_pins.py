@@ -391,6 +391,23 @@ def test_switch_methods(seed):
     assert np.max(np.abs(S1 - S2) / S2) < 1e-13
 
 
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_v_by_qr(mode):
+    """Section 3.4's cheaper V: the refinement without V, then V_X from the QR of X^T U_X as
+    the start of one more Alg. 1 with V accumulated, which converges after one sweep of
+    rotations (a second confirms); the same SVD as accumulating V throughout."""
+    A, _ = inputs.plain_256x128()
+    U0, S0, V0, s0 = oracle.svd(A, mode=mode)
+    U1, S1, V1, s1 = oracle.svd(A, mode=mode, v_by_qr=1)
+    assert s1["status"] == 0 and s1["sweeps_v"] <= 2
+    n = A.shape[1]
+    assert np.max(np.abs(S1 - S0) / S0) < 1e-13
+    assert np.abs(V1.T @ V1 - np.eye(n)).max() < 64 * n * U64
+    assert np.abs(U1.T @ U1 - np.eye(n)).max() < 64 * n * U64
+    assert np.linalg.norm(A - (U1 * S1) @ V1.T) / np.linalg.norm(A) < 1e-14
+    assert np.abs(V1 - V0).max() < 1e-10 and np.abs(U1 - U0).max() < 1e-10
+
+
 def test_mixed_and_plain_agree():
     rng = np.random.default_rng(15)
     A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
