@@ -34,14 +34,15 @@ class _Variant:
             _fields_ = [("tol_alg", creal), ("tol_orth", creal), ("tol_cond_coef", creal),
                         ("trailing_frac", creal), ("tol", creal), ("maxsweep", ctypes.c_int),
                         ("mode", ctypes.c_int), ("precond", ctypes.c_int), ("qrcp", ctypes.c_int),
-                        ("switch_method", ctypes.c_int), ("v_by_qr", ctypes.c_int), ("stop", ctypes.c_int)]
+                        ("switch_method", ctypes.c_int), ("v_by_qr", ctypes.c_int), ("stop", ctypes.c_int),
+                        ("y_tol", creal)]
 
         class Stats(ctypes.Structure):
             _fields_ = [("branch", ctypes.c_int), ("sweeps_low", ctypes.c_int),
                         ("sweeps_work", ctypes.c_int), ("rot_low", ctypes.c_longlong),
                         ("rot_work", ctypes.c_longlong), ("cond_r", creal), ("orth", creal),
                         ("switch_off", creal), ("status", ctypes.c_int), ("precond", ctypes.c_int),
-                        ("sweeps_v", ctypes.c_int)]
+                        ("sweeps_v", ctypes.c_int), ("y2_cols", ctypes.c_int)]
 
             def as_dict(self):
                 d = {name: getattr(self, name) for name, _ in self._fields_}

@@ -44,6 +44,7 @@ void orc_default_params(orc_params* p)
     p->switch_method = 0;
     p->v_by_qr = 0;
     p->stop = 0;
+    p->y_tol = 0.0;
 }
 
 static orc_real nrm2(int len, const orc_real* x)
@@ -313,6 +314,40 @@ static int negligible_sweep(int n, double tol, double cos_max, double tan_max)
     return cos_max < sqrt((double)n) * tol && (double)n * cos_max * tan_max < tol;
 }
 
+/* One pair step of Alg. 1: (p, q) is rotated when |x_q^T x_p| > tol |x_p| |x_q|, with alpha,
+ * beta, gamma recomputed from the columns; the rotation is applied to x_p, x_q and (if vp)
+ * to v_p, v_q (nv rows). Returns 1 if it rotated; tracks the largest cosine and |tan|. */
+static int jacobi_pair(int m, orc_real* xp, orc_real* xq, orc_real* vp, orc_real* vq, int nv, orc_real tol,
+                       double* cos_max, double* tan_max)
+{
+    orc_real alpha = 0.0, beta = 0.0, gamma = 0.0;
+    for (int i = 0; i < m; ++i) {
+        alpha += xp[i] * xp[i];
+        beta += xq[i] * xq[i];
+        gamma += xp[i] * xq[i];
+    }
+    if (!(RFABS(gamma) > tol * RSQRT(alpha) * RSQRT(beta))) return 0;
+    orc_real t = orc_rot_tangent(alpha, beta, gamma);
+    const double cs = (double)(RFABS(gamma) / (RSQRT(alpha) * RSQRT(beta)));
+    if (cs > *cos_max) *cos_max = cs;
+    if (fabs((double)t) > *tan_max) *tan_max = fabs((double)t);
+    orc_real c = 1.0 / RSQRT(1.0 + t * t);
+    orc_real s = c * t;
+    for (int i = 0; i < m; ++i) {
+        orc_real a = xp[i], b = xq[i];
+        xp[i] = c * a - s * b;
+        xq[i] = s * a + c * b;
+    }
+    if (vp) {
+        for (int i = 0; i < nv; ++i) {
+            orc_real a = vp[i], b = vq[i];
+            vp[i] = c * a - s * b;
+            vq[i] = s * a + c * b;
+        }
+    }
+    return 1;
+}
+
 /* Alg. 1 in binary64. Cyclic order (1,2),(1,3),...,(n-1,n) of eq. (cyclic). The pair
  * (p, q) is rotated when |x_q^T x_p| > tol |x_p| |x_q|; a sweep without rotations
  * means convergence (stop = 1), or also a negligible sweep (stop = 0, negligible_sweep).
@@ -327,37 +362,11 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
         double cos_max = 0.0, tan_max = 0.0;
         for (int p = 0; p < n - 1; ++p) {
             for (int q = p + 1; q < n; ++q) {
-                orc_real* xp = &AT(X, 0, p, ldx);
-                orc_real* xq = &AT(X, 0, q, ldx);
-                orc_real alpha = 0.0, beta = 0.0, gamma = 0.0;
-                for (int i = 0; i < m; ++i) {
-                    alpha += xp[i] * xp[i];
-                    beta += xq[i] * xq[i];
-                    gamma += xp[i] * xq[i];
+                if (jacobi_pair(m, &AT(X, 0, p, ldx), &AT(X, 0, q, ldx), V ? &AT(V, 0, p, ldv) : NULL,
+                                V ? &AT(V, 0, q, ldv) : NULL, nv, tol, &cos_max, &tan_max)) {
+                    ++rot;
+                    converged = 0;
                 }
-                if (!(RFABS(gamma) > tol * RSQRT(alpha) * RSQRT(beta))) continue;
-                orc_real t = orc_rot_tangent(alpha, beta, gamma);
-                const double cs = (double)(RFABS(gamma) / (RSQRT(alpha) * RSQRT(beta)));
-                if (cs > cos_max) cos_max = cs;
-                if (fabs((double)t) > tan_max) tan_max = fabs((double)t);
-                orc_real c = 1.0 / RSQRT(1.0 + t * t);
-                orc_real s = c * t;
-                for (int i = 0; i < m; ++i) {
-                    orc_real a = xp[i], b = xq[i];
-                    xp[i] = c * a - s * b;
-                    xq[i] = s * a + c * b;
-                }
-                if (V) {
-                    orc_real* vp = &AT(V, 0, p, ldv);
-                    orc_real* vq = &AT(V, 0, q, ldv);
-                    for (int i = 0; i < nv; ++i) {
-                        orc_real a = vp[i], b = vq[i];
-                        vp[i] = c * a - s * b;
-                        vq[i] = s * a + c * b;
-                    }
-                }
-                ++rot;
-                converged = 0;
             }
         }
         if (!converged && stop == 0 && sweep > 0 && negligible_sweep(n, (double)tol, cos_max, tan_max))
@@ -664,6 +673,35 @@ refine:
      * for the switch) and Alg. 1 with V accumulated from that start on Y = X Q3. */
     {
         orc_real tol = (p.tol > 0.0) ? p.tol : RSQRT((orc_real)n) * U_WORK;
+        long long rot_pre = 0;  /* rotations of the safeguard, added to rot_work at the end */
+        if (p.y_tol > 0.0) {
+            /* Y1/Y2 safeguard: Y1 = the leading columns whose cosines with each other stay
+             * below y_tol, Y2 = the rest; Alg. 1 on Y2 with its columns of V, then one sweep
+             * of the pairs (p in Y1, q in Y2). */
+            int j0 = n;
+            for (int j = 1; j < n && j0 == n; ++j) {
+                const orc_real nj = nrm2(n, &AT(Y, 0, j, n));
+                for (int i = 0; i < j; ++i) {
+                    orc_real g = 0.0;
+                    for (int r = 0; r < n; ++r) g += AT(Y, r, i, n) * AT(Y, r, j, n);
+                    const orc_real ni = nrm2(n, &AT(Y, 0, i, n));
+                    if (RFABS(g) > p.y_tol * ni * nj) { j0 = j; break; }
+                }
+            }
+            s.y2_cols = n - j0;
+            if (j0 < n) {
+                int sw2 = 0;
+                long long rot2 = 0;
+                orc_jacobi(n, n - j0, &AT(Y, 0, j0, n), n, &AT(Vacc, 0, j0, n), n, n, tol, p.maxsweep,
+                           p.stop, &sw2, &rot2);
+                double cmax = 0.0, tmax = 0.0;
+                for (int pp = 0; pp < j0; ++pp)
+                    for (int q = j0; q < n; ++q)
+                        rot2 += jacobi_pair(n, &AT(Y, 0, pp, n), &AT(Y, 0, q, n), &AT(Vacc, 0, pp, n),
+                                            &AT(Vacc, 0, q, n), n, tol, &cmax, &tmax);
+                rot_pre = rot2;
+            }
+        }
         if (!p.v_by_qr) {
             int rc = orc_jacobi(n, n, Y, n, Vacc, n, n, tol, p.maxsweep, p.stop, &s.sweeps_work, &s.rot_work);
             if (rc != 0) s.status = 1;
@@ -709,6 +747,7 @@ refine:
             if (rc != 0) s.status = 1;
             s.rot_work += rot_v;
         }
+        s.rot_work += rot_pre;
     }
 
     /* Sigma = column norms, U_X = normalized columns, sorted descending (Alg. 1). */

@@ -59,6 +59,10 @@ typedef struct {
                               a sweep (not the first) whose rotations were all negligible, as
                               the paper's experiments run it (LAPACK's xGESVJ, Section 7.1);
                               1 -> only after a sweep without rotations (Alg. 1 as printed) */
+    orc_real y_tol;          /* > 0: the Y1/Y2 safeguard of Section 3.4 before the refinement:
+                              Y2 = the columns from the first one (in the switch's order) whose
+                              largest cosine with an earlier column exceeds y_tol; Alg. 1 on Y2,
+                              then one sweep of the pairs between Y1 and Y2. 0: off (default) */
 } orc_params;
 
 /* What the driver did (per call). */
@@ -76,6 +80,7 @@ typedef struct {
     int status;            /* 0 ok, 1 FP64 sweeps hit maxsweep, 2 non-finite input, <0 bad argument */
     int precond;           /* the Jacobi input that ran: 0 R^T, 1 R, 2 L */
     int sweeps_v;          /* v_by_qr = 1: sweeps of the final Alg. 1 with V */
+    int y2_cols;           /* columns in the Y2 block of the safeguard (0: not activated) */
 } orc_stats;
 
 void orc_default_params(orc_params* p);

@@ -408,6 +408,23 @@ def test_v_by_qr(mode):
     assert np.abs(V1 - V0).max() < 1e-10 and np.abs(U1 - U0).max() < 1e-10
 
 
+def test_y1_y2_safeguard():
+    """Section 3.4's safeguard: at the paper's orthogonality level (1e-5) the switch leaves Y
+    orthogonal enough that Y2 is empty (\"rarely activated\"), and the result is the default's
+    bit for bit; forced on with a tiny threshold it rotates inside Y2 and between Y1 and Y2
+    first, and the refinement reaches the same SVD."""
+    A, _ = inputs.plain_256x128()
+    U0, S0, V0, s0 = oracle.svd(A, mode="mixed")
+    U1, S1, V1, s1 = oracle.svd(A, mode="mixed", y_tol=1e-5)
+    assert s1["y2_cols"] == 0 and np.array_equal(S1, S0) and np.array_equal(V1, V0)
+    U2, S2, V2, s2 = oracle.svd(A, mode="mixed", y_tol=1e-12)
+    assert s2["y2_cols"] > 0 and s2["status"] == 0 and s2["rot_work"] > 0
+    n = A.shape[1]
+    assert np.max(np.abs(S2 - S0) / S0) < 1e-13
+    assert np.abs(V2.T @ V2 - np.eye(n)).max() < 64 * n * U64
+    assert np.abs(V2 - V0).max() < 1e-10
+
+
 def test_mixed_and_plain_agree():
     rng = np.random.default_rng(15)
     A = inputs.known_sigma(rng, 90, 64, np.logspace(0, -5, 64))
