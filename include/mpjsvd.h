@@ -6,12 +6,16 @@
  * What is computed: the thin SVD A = U diag(S) V^T of a dense real m x n matrix
  * (m >= n), to high relative accuracy, by Algorithm 4 of the paper:
  *   1. QR preconditioning (Section 3.1): Householder QR with column pivoting of A
- *      (optionally preceded by a plain QR when m > n), A P = Q R;
+ *      (optionally preceded by a plain QR when m > n), A P = Q R; by default the
+ *      mixed-precision RRQR of Alg. 5 (pivot order from a binary32 search, then the
+ *      binary64 QR of A P);
  *   2. the special-case tests of Section 3.5 (cond_R, small trailing columns, orth);
  *   3. a binary32 one-sided Jacobi SVD (Alg. 1, Section 3.2) of the triangular factor,
  *      left singular vectors only;
  *   4. the precision switch of Section 3.3: B = X^T U_low, B = Q R2, Y = X Q;
- *   5. binary64 one-sided Jacobi refinement of Y (Alg. 1, Section 3.4) accumulating V;
+ *   5. binary64 one-sided Jacobi refinement of Y (Alg. 1, Section 3.4) accumulating V
+ *      (both Jacobi stages stop as params.stop says: by default also after a sweep whose
+ *      rotations were all negligible, as the paper's experiments run Alg. 1);
  *   6. Sigma = column norms, U_X = normalized columns, sorted descending; U and V are
  *      assembled from the factors (Alg. 4, last line).
  * Every stage runs as hand-written CUDA kernels on the handle's stream.
