@@ -65,10 +65,13 @@ def test_struct_layouts_match_header(tmp_path):
 
 
 def test_default_params_are_the_papers(lib_path):
+    """The tunables of Section 7.1 and the documented defaults of the algorithm choices
+    (host only: mpjsvd_default_params makes no CUDA call)."""
     from paper_2209_04626_gb300 import mpjsvd
     p = mpjsvd.mpjsvd_default_params()
     assert (p.tol_alg, p.tol_orth, p.tol_cond_coef) == (1e-2, 1e-5, 1.5)
-    assert p.maxsweep == 30 and p.mode == 0
+    assert p.trailing_frac == 0.25 and p.maxsweep == 30 and p.block_w == 0
+    assert p.mode == 0 and p.precond == 0 and p.qr_first == 0 and p.qrcp == 0 and p.stop == 0
 
 
 def test_argument_validation_without_gpu(lib_path):
