@@ -91,6 +91,9 @@ typedef struct {
     int qrcp;             /* MPJSVD_QRCP_*; Alg. 5 falls back to binary64 when the binary32
                              matrix does not fit the resident kernel (stats.qrcp tells) */
     int stop;             /* MPJSVD_STOP_* */
+    int wait_limit_ms;    /* 4000: every bounded device wait of a call (a grid barrier, a block
+                             hand-off between CTAs) gives up after this many milliseconds and
+                             records MPJSVD_STATUS_TIMEOUT; 1 .. 600000 */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
@@ -114,6 +117,9 @@ typedef struct {
     float ms_final;
     int launches;         /* CUDA kernels the call launched (gated-off stages included) */
     int qrcp;             /* the RRQR that ran: MPJSVD_QRCP_MIXED or MPJSVD_QRCP_F64 */
+    int n_flagged;        /* near-degenerate count of the handle's last mpjsvd_svd_backward
+                             (pairs with |s_i - s_j| <= gap_tol max(s_i, s_j) plus s_i <= 2^-53 s_0);
+                             -1 if the handle has run none */
 } mpjsvd_stats;
 
 /* Fill *p with the defaults. Returns 0, or -1 if p is NULL. */
@@ -173,6 +179,21 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
                         const double* V, const double* gU, const double* gS, const double* gV,
                         double* gA, double gap_tol, int* n_flagged);
 
+/* Adjoints of a batch of thin SVDs (the differentiation workload's many small matrices) in
+ * one launch, one CTA per matrix; the formula and the flags of mpjsvd_svd_backward.
+ *   m, n      : HOST arrays of length batch, 1 <= n_i <= m_i <= 4096, n_i <= 512
+ *   U, S, V, gA : DEVICE arrays of length batch holding device pointers (U_i m_i x n_i, leading
+ *               dimension m_i; V_i n_i x n_i; gA_i m_i x n_i, leading dimension m_i)
+ *   gU, gS, gV : DEVICE arrays of device pointers or NULL (all zero); a NULL entry is a zero
+ *               cotangent for that matrix
+ *   n_flagged : DEVICE int array of length batch: per matrix, the near-degenerate count
+ * Asynchronous on the handle's stream; uses the handle's adjoint workspace. */
+int mpjsvd_svd_backward_batched(mpjsvd_handle h, int batch, const int* m, const int* n,
+                                const double* const* U, const double* const* S,
+                                const double* const* V, const double* const* gU,
+                                const double* const* gS, const double* const* gV,
+                                double* const* gA, double gap_tol, int* n_flagged);
+
 /* Allocation-free thin SVD of one small matrix (the paper has no counterpart: this is a
  * deployment variant of mpjsvd_svd). It takes no handle and calls no cudaMalloc, cudaFree or
  * allocating library routine, for callers that cannot allocate device memory: code whose
@@ -184,13 +205,18 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
  *          mpjsvd_last_error())
  *   A, U, S, V, lda, tol : as in mpjsvd_svd (device pointers, default parameters,
  *          MPJSVD_MODE_AUTO)
+ *   status : DEVICE int, may be NULL; written on the stream after the last stage with the
+ *          call's MPJSVD_STATUS_* bits (read it after synchronizing the stream). A call whose
+ *          status has MPJSVD_STATUS_NONFINITE or MPJSVD_STATUS_TIMEOUT set produced no
+ *          meaningful U, S, V (they are filled with NaN)
  *   cuda_stream : the stream the work is enqueued on (cudaStream_t; NULL = legacy stream)
- * The first call on a device looks up the scratch array's device address (once per device,
- * with that device current); make that first call before any stream capture. Every call
- * shares the scratch array: calls that overlap on the GPU (other streams, other host threads)
- * race and must be ordered by the caller. Numeric status is not reported (no handle). */
+ * The call does not block: 0 means "arguments valid, work enqueued". The first call on a
+ * device looks up the scratch array's device address (once per device, with that device
+ * current); make that first call before any stream capture. Every call shares the scratch
+ * array: calls that overlap on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller. */
 int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S, double* V,
-                       double tol, void* cuda_stream);
+                       double tol, int* status, void* cuda_stream);
 
 /* Householder QR of one matrix, in place (the QR preconditioning of Section 3.1 and the QR
  * of the precision switch of Section 3.3 as a standalone call; blocked, compact-WY form).
@@ -221,6 +247,22 @@ int mpjsvd_geqp3(mpjsvd_handle h, int m, int n, double* A, int lda, int* jpvt, d
  * first ncols columns of the identity. */
 int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, int lda,
                    const double* tau, double* C, int ldc);
+
+/* Measurement utility (not part of the paper): the FP64 FMA throughput of the current GPU in
+ * TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on every SM, timed with
+ * CUDA events on cuda_stream (best of three launches after a warm-up; about 0.1 s). This is
+ * the denominator of the FP64 roofline fractions. Returns 0, -2 for a NULL tflops,
+ * MPJSVD_ERR_CUDA. Synchronizes cuda_stream. */
+int mpjsvd_measure_fp64_peak(void* cuda_stream, double* tflops);
+
+/* Failure-detection check (not part of the paper): enqueue on the handle's stream a kernel
+ * whose cross-CTA waits can never be satisfied (a block hand-off on a counter that nothing
+ * releases, and a grid barrier that one CTA never reaches). Both waits are the library's
+ * own bounded waits: after params.wait_limit_ms they give up, record MPJSVD_STATUS_TIMEOUT
+ * and return, so the kernel exits and the handle stays usable. The status is then read with
+ * mpjsvd_get_stats(). Uses the handle's workspace. Returns 0 (enqueued), -1 for a NULL
+ * handle, MPJSVD_ERR_CUDA. */
+int mpjsvd_selftest_timeout(mpjsvd_handle h);
 
 /* Synchronize the handle's stream and copy the stats of the last mpjsvd_svd call. */
 int mpjsvd_get_stats(mpjsvd_handle h, mpjsvd_stats* st);

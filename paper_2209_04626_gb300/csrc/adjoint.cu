@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <new>
 
 #include "common.cuh"
 #include "gemm.cuh"
@@ -125,12 +126,141 @@ int svd_backward(mpjsvd_ctx* h, int m, int n, const double* U, const double* S, 
     k_adj_flags<<<std::max(1, (n + 255) / 256), 256, 0, s>>>(n, S, gap_tol, count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("adjoint kernels", e);
+    h->last_flag_dev = count;
     if (n_flagged) {
         e = cudaMemcpyAsync(n_flagged, count, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail("adjoint flag copy", e);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail("adjoint sync", e);
     }
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Batched adjoint: one CTA per matrix, the same formula as svd_backward. Small matrices (the
+// differentiation workload's 64 x 32): M1 = U^T gU, M2 = V^T gV, K' and T = U K' + gU S^-1
+// live in the CTA's slot of a global scratch (L2-resident at these sizes); gA = T V^T is
+// written directly.
+// ------------------------------------------------------------------------------------
+
+struct BwdPtrs {
+    const double* const* U;
+    const double* const* S;
+    const double* const* V;
+    const double* const* gU;  // may be null (every cotangent zero), entries may be null
+    const double* const* gS;
+    const double* const* gV;
+    double* const* gA;
+};
+
+__global__ void __launch_bounds__(256) k_adj_batched(BwdPtrs P, const int* dims, double* scratch,
+                                                     size_t slot_doubles, double gap_tol, int* flags)
+{
+    const int b = blockIdx.x;
+    const int m = dims[2 * b], n = dims[2 * b + 1];
+    const double* U = P.U[b];
+    const double* S = P.S[b];
+    const double* V = P.V[b];
+    const double* gU = P.gU ? P.gU[b] : nullptr;
+    const double* gS = P.gS ? P.gS[b] : nullptr;
+    const double* gV = P.gV ? P.gV[b] : nullptr;
+    double* gA = P.gA[b];
+    double* M1 = scratch + slot_doubles * (size_t)b;
+    double* M2 = M1 + (size_t)n * n;
+    double* K = M2 + (size_t)n * n;
+    double* T = K + (size_t)n * n;  // m x n
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const size_t nn = (size_t)n * n;
+    // M1 = U^T gU (n x n, K = m), M2 = V^T gV (n x n, K = n)
+    for (size_t e = tid; e < nn; e += nt) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double a = 0.0, c = 0.0;
+        if (gU)
+            for (int k = 0; k < m; ++k) a = fma(U[cm(k, i, m)], gU[cm(k, j, m)], a);
+        if (gV)
+            for (int k = 0; k < n; ++k) c = fma(V[cm(k, i, n)], gV[cm(k, j, n)], c);
+        M1[e] = a;
+        M2[e] = c;
+    }
+    __syncthreads();
+    // K' (same entries as k_adj_core)
+    for (size_t e = tid; e < nn; e += nt) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        const double si = S[i], sj = S[j];
+        const double m1ij = M1[e];
+        double v;
+        if (i == j) {
+            v = (gS ? gS[i] : 0.0) - m1ij / sj;
+        } else {
+            const double f = 1.0 / (sj * sj - si * si);
+            v = f * (m1ij - M1[cm(j, i, n)]) * sj + si * f * (M2[e] - M2[cm(j, i, n)]) - m1ij / sj;
+        }
+        K[e] = v;
+    }
+    __syncthreads();
+    // T = U K' + gU S^-1
+    for (size_t e = tid; e < (size_t)m * n; e += nt) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        double t = gU ? gU[e] / S[j] : 0.0;
+        for (int k = 0; k < n; ++k) t = fma(U[cm(i, k, m)], K[cm(k, j, n)], t);
+        T[e] = t;
+    }
+    __syncthreads();
+    // gA = T V^T
+    for (size_t e = tid; e < (size_t)m * n; e += nt) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        double t = 0.0;
+        for (int k = 0; k < n; ++k) t = fma(T[cm(i, k, m)], V[cm(j, k, n)], t);
+        gA[e] = t;
+    }
+    // near-degenerate pairs and tiny singular values: counted, never clamped
+    int local = 0;
+    const double u = 1.1102230246251565e-16;
+    for (int i = tid; i < n; i += nt) {
+        const double si = S[i];
+        if (si <= u * S[0]) ++local;
+        for (int j = i + 1; j < n; ++j)
+            if (fabs(si - S[j]) <= gap_tol * fmax(si, S[j])) ++local;
+    }
+    if (local) atomicAdd(&flags[b], local);
+}
+
+int svd_backward_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n,
+                         const double* const* U, const double* const* S, const double* const* V,
+                         const double* const* gU, const double* const* gS, const double* const* gV,
+                         double* const* gA, double gap_tol, int* n_flagged)
+{
+    int mmax = 0, nmax = 0;
+    for (int b = 0; b < batch; ++b) {
+        mmax = std::max(mmax, m[b]);
+        nmax = std::max(nmax, n[b]);
+    }
+    const size_t slot = 3 * (size_t)nmax * nmax + (size_t)mmax * nmax;
+    const size_t dims_bytes = (sizeof(int) * 2 * (size_t)batch + 255) & ~size_t(255);
+    int rc = ensure_buffer(&h->aws, &h->aws_bytes, dims_bytes + sizeof(double) * slot * (size_t)batch);
+    if (rc) return rc;
+    int* dims = (int*)h->aws;
+    double* scratch = (double*)((char*)h->aws + dims_bytes);
+    // the sizes: host arrays, packed and copied once (from pageable memory the copy has taken
+    // the data before cudaMemcpyAsync returns, so the packed array can be freed at once)
+    int* packed = new (std::nothrow) int[2 * (size_t)batch];
+    if (!packed) return MPJSVD_ERR_NOMEM;
+    for (int b = 0; b < batch; ++b) {
+        packed[2 * b] = m[b];
+        packed[2 * b + 1] = n[b];
+    }
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaMemcpyAsync(dims, packed, sizeof(int) * 2 * (size_t)batch,
+                                    cudaMemcpyHostToDevice, s);
+    delete[] packed;
+    if (e != cudaSuccess) return cuda_fail("batched adjoint: sizes", e);
+    e = cudaMemsetAsync(n_flagged, 0, sizeof(int) * (size_t)batch, s);
+    if (e != cudaSuccess) return cuda_fail("batched adjoint: flags", e);
+    BwdPtrs P{U, S, V, gU, gS, gV, gA};
+    k_adj_batched<<<batch, 256, 0, s>>>(P, dims, scratch, slot, gap_tol, n_flagged);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("batched adjoint launch", e);
+    h->last_flag_dev = nullptr;
     return 0;
 }
 

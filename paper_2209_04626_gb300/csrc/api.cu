@@ -26,6 +26,24 @@ int cuda_fail(const char* where, cudaError_t e)
     return MPJSVD_ERR_CUDA;
 }
 
+// Zero the per-call state block and store the call's wait limit in it (one small kernel).
+static __global__ void k_state_reset(DevState* st, unsigned long long spin_ns)
+{
+    for (size_t i = threadIdx.x; i < sizeof(DevState) / 4; i += blockDim.x) ((int*)st)[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) st->spin_ns = spin_ns;
+}
+
+int state_reset(mpjsvd_ctx* h, void* st)
+{
+    const unsigned long long ns = (unsigned long long)h->params.wait_limit_ms * 1000000ull;
+    k_state_reset<<<1, 256, 0, h->stream>>>((DevState*)st, ns);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("state reset", e);
+    ++h->launch_count;
+    return 0;
+}
+
 int ensure_buffer(void** buf, size_t* cur, size_t bytes)
 {
     if (*buf && *cur >= bytes) return 0;
@@ -67,6 +85,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->timing = 0;
     p->qrcp = MPJSVD_QRCP_MIXED;
     p->stop = MPJSVD_STOP_XGESVJ;
+    p->wait_limit_ms = 4000;
     return 0;
 }
 
@@ -79,6 +98,7 @@ static int check_params(const mpjsvd_params* p)
     if (p->qrcp < 0 || p->qrcp > 1) return 1;
     if (p->stop < 0 || p->stop > 1) return 1;
     if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
+    if (p->wait_limit_ms < 1 || p->wait_limit_ms > 600000) return 1;
     return 0;
 }
 
@@ -213,6 +233,30 @@ int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const do
     if (!gA) return -10;
     if (!(gap_tol >= 0.0)) return -11;
     return svd_backward(h, m, n, U, S, V, gU, gS, gV, gA, gap_tol, n_flagged);
+}
+
+int mpjsvd_svd_backward_batched(mpjsvd_handle h, int batch, const int* m, const int* n,
+                                const double* const* U, const double* const* S,
+                                const double* const* V, const double* const* gU,
+                                const double* const* gS, const double* const* gV,
+                                double* const* gA, double gap_tol, int* n_flagged)
+{
+    if (!h) return -1;
+    if (batch < 0) return -2;
+    if (batch == 0) return 0;
+    if (!m) return -3;
+    if (!n) return -4;
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] < 1 || n[i] > 512) return -4;
+        if (m[i] < n[i] || m[i] > 4096) return -3;
+    }
+    if (!U) return -5;
+    if (!S) return -6;
+    if (!V) return -7;
+    if (!gA) return -11;
+    if (!(gap_tol >= 0.0)) return -12;
+    if (!n_flagged) return -13;
+    return svd_backward_batched(h, batch, m, n, U, S, V, gU, gS, gV, gA, gap_tol, n_flagged);
 }
 
 int mpjsvd_geqrf(mpjsvd_handle h, int m, int n, double* A, int lda, double* tau)

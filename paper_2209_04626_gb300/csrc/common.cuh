@@ -1,9 +1,10 @@
 // common.cuh -- device helpers shared by the mpjsvd kernels (sm_103a).
 //
 // Matrices are column-major FP64 (LAPACK convention) unless a name says otherwise.
-// Every wait in device code is bounded in time: a grid barrier gives up after
-// kSpinLimitNs, records MPJSVD_STATUS_TIMEOUT in the call's status word and returns
-// false, so the kernel can exit and the context stays usable.
+// Every wait in device code is bounded in time: a grid barrier gives up after the call's
+// limit (params.wait_limit_ms, stored in DevState::spin_ns; kSpinLimitNs when unset),
+// records MPJSVD_STATUS_TIMEOUT in the call's status word and returns false, so the kernel
+// can exit and the context stays usable.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,7 +15,7 @@
 namespace mpj {
 
 constexpr int kWarp = 32;
-constexpr uint64_t kSpinLimitNs = 4000000000ull;  // 4 s
+constexpr uint64_t kSpinLimitNs = 4000000000ull;  // 4 s: the limit when none is set
 
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
@@ -45,7 +46,15 @@ struct DevState {
     unsigned long long cand_rec[512];      // Alg. 5: per-CTA step records (tag, column, norm) x parity
     unsigned mx_cos[2][64];                // binary32 bits: largest cosine among the rotated pairs, [phase][sweep]
     unsigned mx_tan[2][64];                // binary32 bits: largest |tan| of the rotations, [phase][sweep]
+    unsigned long long spin_ns;            // limit of every bounded wait of the call (0: kSpinLimitNs)
 };
+
+// The call's wait limit in nanoseconds.
+__device__ __forceinline__ uint64_t spin_limit_ns(const DevState* st)
+{
+    const uint64_t v = *(volatile const unsigned long long*)&st->spin_ns;
+    return v ? v : kSpinLimitNs;
+}
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative
 // stage that gave up on a bounded wait. Later stages then return at once.
@@ -81,11 +90,11 @@ __device__ __forceinline__ bool grid_sync(DevState* st)
             st->bar_count = 0;
             asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&st->bar_gen), "r"(gen + 1) : "memory");
         } else {
-            const uint64_t t0 = globaltimer_ns();
+            const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
             unsigned spins = 0;
             while (ld_acquire_gpu(&st->bar_gen) == gen) {
                 if ((++spins & 1023u) == 0) {
-                    if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                    if (globaltimer_ns() - t0 > lim) {
                         atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
                         ok = 0;
                         break;

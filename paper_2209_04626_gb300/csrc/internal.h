@@ -31,6 +31,7 @@ struct mpjsvd_ctx {
     int last_block_w_low, last_block_w_work;
     int launch_count;  // kernels launched by the last call
     int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
+    int* last_flag_dev;  // device count of near-degenerate flags of the last svd_backward
     // the blocked QR's look-ahead: the critical chain (panels and the updates of the next
     // panel) on a high-priority stream, the wide trailing updates on a low-priority one;
     // both fork from and join back into `stream` through events
@@ -46,6 +47,10 @@ namespace mpj {
 // error bookkeeping (thread-local text of the last CUDA error)
 void set_last_error(const char* where, cudaError_t e);
 int cuda_fail(const char* where, cudaError_t e);
+
+// zero the per-call state block (DevState) on the handle's stream and store the call's wait
+// limit in it
+int state_reset(mpjsvd_ctx* h, void* st);
 
 // grow a device buffer to at least `bytes`
 int ensure_buffer(void** buf, size_t* cur, size_t bytes);
@@ -93,5 +98,9 @@ int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int*
 int svd_backward(mpjsvd_ctx* h, int m, int n, const double* U, const double* S, const double* V,
                  const double* gU, const double* gS, const double* gV, double* gA, double gap_tol,
                  int* n_flagged);
+int svd_backward_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n,
+                         const double* const* U, const double* const* S, const double* const* V,
+                         const double* const* gU, const double* const* gS, const double* const* gV,
+                         double* const* gA, double gap_tol, int* n_flagged);
 
 }  // namespace mpj

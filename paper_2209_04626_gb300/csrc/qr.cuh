@@ -358,10 +358,10 @@ __device__ __forceinline__ bool wait_flag(const int* flag, DevState* st)
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        uint64_t t0 = globaltimer_ns();
+        const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
         unsigned int spins = 0;
         while (*(volatile const int*)flag == 0) {
-            if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kSpinLimitNs) {
+            if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > lim) {
                 atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
                 ok = 0;
                 break;

@@ -677,9 +677,9 @@ int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau)
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), h->stream);
-    if (e != cudaSuccess) return cuda_fail("memset state", e);
     h->launch_count = 0;
+    rc = state_reset(h, st);
+    if (rc) return rc;
     return bqr_factor(h, m, n, A, lda, tau, (double*)h->ws, st, -1);
 }
 
@@ -690,9 +690,9 @@ int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int ld
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), h->stream);
-    if (e != cudaSuccess) return cuda_fail("memset state", e);
     h->launch_count = 0;
+    rc = state_reset(h, st);
+    if (rc) return rc;
     return bqr_apply(h, m, ncols, k, A, lda, tau, C, ldc, false, (double*)h->ws, st, -1);
 }
 

@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kRegWarps * 32)
                 }
                 if ((++spins & 255u) == 0) {
                     if (*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) break;
-                    if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                    if (globaltimer_ns() - t0 > spin_limit_ns(st)) {
                         if (lane == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
                         break;
                     }
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(kRegWarps * 32)
                 if (ok) break;
                 if ((++spins & 255u) == 0) {
                     if ((*(volatile int*)&st->status & MPJSVD_STATUS_TIMEOUT) ||
-                        globaltimer_ns() - t0 > kSpinLimitNs) {
+                        globaltimer_ns() - t0 > spin_limit_ns(st)) {
                         bad = true;
                         break;
                     }

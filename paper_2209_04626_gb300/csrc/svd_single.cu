@@ -658,8 +658,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     cudaError_t e;
     h->launch_count = 0;
 
-    e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
-    if (e != cudaSuccess) return cuda_fail("memset state", e);
+    if ((rc = state_reset(h, st))) return rc;
     e = cudaMemsetAsync(bits, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail("memset bits", e);
     record(h, 0);
@@ -820,8 +819,8 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
     cudaStream_t s = h->stream;
     const int egrid = h->num_sms * 4;
     h->launch_count = 0;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
-    if (e != cudaSuccess) return cuda_fail("memset state", e);
+    if ((rc = state_reset(h, st))) return rc;
+    cudaError_t e;
     bool mixed_done = false;
     if (h->params.qrcp == MPJSVD_QRCP_MIXED && bqr_nb(m) > 0 && m <= 12480) {
         rc = launch_qrcp_low(h, m, n, A, lda, jpvt, (float*)bcast, st);
@@ -865,6 +864,11 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     r.block_w_work = h->last_block_w_work;
     r.launches = h->launch_count;
     r.qrcp = h->last_qrcp;
+    r.n_flagged = -1;
+    if (h->last_flag_dev) {
+        e = cudaMemcpy(&r.n_flagged, h->last_flag_dev, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail("stats: flag count", e);
+    }
     if (h->params.timing && h->have_events) {
         float* t[6] = {&r.ms_qr, &r.ms_branch, &r.ms_low, &r.ms_switch, &r.ms_work, &r.ms_final};
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(t[i], h->ev[i], h->ev[i + 1]);
@@ -911,41 +915,61 @@ static int noalloc_scratch(int dev, void** out)
     return 0;
 }
 
+// status[0] = the call's MPJSVD_STATUS_* bits, enqueued after the last stage.
+__global__ void k_copy_status(const DevState* st, int* status)
+{
+    *status = *(volatile const int*)&st->status;
+}
+
 static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S, double* V,
-                       double tol, cudaStream_t stream)
+                       double tol, int* status, cudaStream_t stream)
 {
     if (m > kNoAllocMaxM || n > kNoAllocMaxN)
         return cuda_fail("mpjsvd_svd_noalloc: m > 512 or n > 256 exceeds the static scratch",
                          cudaErrorInvalidValue);
-    const size_t state_bytes = align256(sizeof(DevState));
-    SingleLayout L = single_layout(m, n, false);
-    if (state_bytes + L.total > kNoAllocBytes)
-        return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
-                         cudaErrorInvalidValue);
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: cudaGetDevice", e);
-    void* base = nullptr;
-    int rc = noalloc_scratch(dev, &base);
-    if (rc) return rc;
     mpjsvd_ctx ctx;
     memset(&ctx, 0, sizeof(ctx));
     ctx.device = dev;
+    mpjsvd_default_params(&ctx.params);
+    // the workspace svd_single will ask for, from the same parameters it reads
+    const size_t state_bytes = align256(sizeof(DevState));
+    const size_t need = single_layout(m, n, ctx.params.qr_first && m > n).total;
+    if (state_bytes + need > kNoAllocBytes)
+        return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
+                         cudaErrorInvalidValue);
+    void* base = nullptr;
+    int rc = noalloc_scratch(dev, &base);
+    if (rc) return rc;
     e = cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: SM count", e);
     ctx.stream = stream;
-    mpjsvd_default_params(&ctx.params);
     ctx.dstate = base;
-    ctx.ws = (char*)base + state_bytes;
+    void* const ws = (char*)base + state_bytes;
+    ctx.ws = ws;
     ctx.ws_bytes = kNoAllocBytes - state_bytes;  // ensure_buffer never allocates below this
     ctx.have_events = false;
-    return svd_single(&ctx, m, n, A, lda, U, S, V, tol);
+    rc = svd_single(&ctx, m, n, A, lda, U, S, V, tol);
+    // a workspace request above ws_bytes would have replaced the static array by a cudaMalloc:
+    // the size check above rules that out; if it ever did not, fail instead of continuing
+    if (ctx.ws != ws || ctx.ws_bytes != kNoAllocBytes - state_bytes)
+        return cuda_fail("mpjsvd_svd_noalloc: the workspace left the static scratch",
+                         cudaErrorInvalidValue);
+    if (rc) return rc;
+    if (status) {
+        k_copy_status<<<1, 1, 0, stream>>>((const DevState*)base, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail("mpjsvd_svd_noalloc: status copy", e);
+    }
+    return 0;
 }
 
 }  // namespace mpj
 
 extern "C" int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double* U, double* S,
-                                  double* V, double tol, void* cuda_stream)
+                                  double* V, double tol, int* status, void* cuda_stream)
 {
     if (m < 1 || m < n) return -1;
     if (n < 1) return -2;
@@ -965,5 +989,5 @@ extern "C" int mpjsvd_svd_noalloc(int m, int n, const double* A, int lda, double
     if (!S) return -6;
     if (!V) return -7;
     if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -8;
-    return mpj::svd_noalloc(m, n, A, lda, U, S, V, tol, (cudaStream_t)cuda_stream);
+    return mpj::svd_noalloc(m, n, A, lda, U, S, V, tol, status, (cudaStream_t)cuda_stream);
 }

@@ -641,7 +641,7 @@ __device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj,
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint64_t t0 = globaltimer_ns();
+        const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
         unsigned spins = 0;
         // tight acquire spin (the wait is usually a few microseconds), time-bounded
         while (ld_acquire_u32(ver + bi) < R || ld_acquire_u32(ver + bj) < R) {
@@ -650,7 +650,7 @@ __device__ __forceinline__ bool wait_blocks(const unsigned* ver, int bi, int bj,
                     ok = 0;
                     break;
                 }
-                if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                if (globaltimer_ns() - t0 > lim) {
                     atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
                     ok = 0;
                     break;

@@ -10,6 +10,7 @@ held here as a torch tensor of shape (m, n) with strides (1, m) (``colmajor`` ma
 """
 import ctypes
 import os
+import warnings
 
 import torch
 
@@ -26,7 +27,8 @@ STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2
 EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsvd_set_params",
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
            "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
-           "mpjsvd_apply_q", "mpjsvd_geqp3"]
+           "mpjsvd_apply_q", "mpjsvd_geqp3", "mpjsvd_selftest_timeout",
+           "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak"]
 
 
 class Params(ctypes.Structure):
@@ -34,7 +36,7 @@ class Params(ctypes.Structure):
                 ("tol_cond_coef", ctypes.c_double), ("trailing_frac", ctypes.c_double),
                 ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
-                ("qrcp", ctypes.c_int), ("stop", ctypes.c_int)]
+                ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -45,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("block_w_work", ctypes.c_int), ("ms_qr", ctypes.c_float),
                 ("ms_branch", ctypes.c_float), ("ms_low", ctypes.c_float),
                 ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
-                ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int)]
+                ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int),
+                ("n_flagged", ctypes.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -79,10 +82,14 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
     L.mpjsvd_destroy.argtypes = [_vp]
     L.mpjsvd_last_error.restype = ctypes.c_char_p
-    L.mpjsvd_svd_noalloc.argtypes = [_i, _i, _vp, _i, _vp, _vp, _vp, _d, _vp]
+    L.mpjsvd_svd_noalloc.argtypes = [_i, _i, _vp, _i, _vp, _vp, _vp, _d, _vp, _vp]
     L.mpjsvd_geqrf.argtypes = [_vp, _i, _i, _vp, _i, _vp]
     L.mpjsvd_apply_q.argtypes = [_vp, _i, _i, _i, _vp, _i, _vp, _vp, _i]
     L.mpjsvd_geqp3.argtypes = [_vp, _i, _i, _vp, _i, _vp, _vp]
+    L.mpjsvd_selftest_timeout.argtypes = [_vp]
+    L.mpjsvd_measure_fp64_peak.argtypes = [_vp, ctypes.POINTER(_d)]
+    L.mpjsvd_svd_backward_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                              _vp, _d, _vp]
     _lib = L
     return L
 
@@ -145,6 +152,13 @@ def mpjsvd_svd_backward(h, m, n, U_ptr, S_ptr, V_ptr, gU_ptr, gS_ptr, gV_ptr, gA
     return rc, nf.value
 
 
+def mpjsvd_svd_backward_batched(h, batch, m_host, n_host, U_ptrs, S_ptrs, V_ptrs, gU_ptrs,
+                                gS_ptrs, gV_ptrs, gA_ptrs, gap_tol, flags_ptr):
+    return load_library().mpjsvd_svd_backward_batched(
+        h, batch, _vp(m_host), _vp(n_host), _vp(U_ptrs), _vp(S_ptrs), _vp(V_ptrs), _vp(gU_ptrs),
+        _vp(gS_ptrs), _vp(gV_ptrs), _vp(gA_ptrs), gap_tol, _vp(flags_ptr))
+
+
 def mpjsvd_get_stats(h):
     st = Stats()
     _check(load_library().mpjsvd_get_stats(h, ctypes.byref(st)), "mpjsvd_get_stats")
@@ -160,11 +174,25 @@ def mpjsvd_last_error():
     return load_library().mpjsvd_last_error().decode()
 
 
-def mpjsvd_svd_noalloc(m, n, A_ptr, lda, U_ptr, S_ptr, V_ptr, tol=0.0, stream=None):
-    """Allocation-free SVD for m <= 512, n <= 256 (static device scratch, no handle)."""
+def mpjsvd_svd_noalloc(m, n, A_ptr, lda, U_ptr, S_ptr, V_ptr, tol=0.0, status_ptr=None,
+                       stream=None):
+    """Allocation-free SVD for m <= 512, n <= 256 (static device scratch, no handle).
+    status_ptr: device int (or None) that receives the call's status bits."""
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     return load_library().mpjsvd_svd_noalloc(m, n, _vp(A_ptr), lda, _vp(U_ptr), _vp(S_ptr),
-                                             _vp(V_ptr), tol, _vp(s))
+                                             _vp(V_ptr), tol, _vp(status_ptr), _vp(s))
+
+
+def mpjsvd_measure_fp64_peak(stream=None):
+    """FP64 FMA throughput of the current GPU in TFLOP/s (the FP64 roofline denominator)."""
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    v = _d(0.0)
+    _check(load_library().mpjsvd_measure_fp64_peak(_vp(s), ctypes.byref(v)), "mpjsvd_measure_fp64_peak")
+    return v.value
+
+
+def mpjsvd_selftest_timeout(h):
+    return load_library().mpjsvd_selftest_timeout(h)
 
 
 def mpjsvd_geqrf(h, m, n, A_ptr, lda, tau_ptr):
@@ -309,7 +337,42 @@ class Handle:
                                      gV.data_ptr() if gV is not None else None,
                                      gA.data_ptr(), gap_tol)
         _check(rc, "mpjsvd_svd_backward")
+        self.last_n_flagged = nf
         return gA, nf
+
+    def backward_batched(self, Us, Ss, Vs, gUs=None, gSs=None, gVs=None, gap_tol=1e-3):
+        """Adjoints of a batch of thin SVDs in one launch. Each g* is a list (entries may be
+        None) or None. Returns (list of gA, device int tensor of per-matrix flag counts)."""
+        import numpy as np
+        dev = Us[0].device
+        b = len(Us)
+        m = np.array([U.shape[0] for U in Us], dtype=np.int32)
+        n = np.array([U.shape[1] for U in Us], dtype=np.int32)
+        cm = lambda t: (colmajor(t, dev) if t.dim() == 2 and not _is_colmajor(t) else t)
+        Us = [cm(U) for U in Us]
+        Vs = [cm(V) for V in Vs]
+        gAs = [empty_colmajor(int(mi), int(ni), dev) for mi, ni in zip(m, n)]
+
+        def ptrs(ts):
+            if ts is None:
+                return None
+            ts = [None if t is None else (cm(t) if t.dim() == 2 else t.contiguous()) for t in ts]
+            keep.append(ts)
+            return torch.tensor([0 if t is None else t.data_ptr() for t in ts], dtype=torch.int64,
+                                device=dev)
+
+        keep = []
+        pU, pS, pV, pA = ptrs(Us), ptrs(Ss), ptrs(Vs), ptrs(gAs)
+        pgU, pgS, pgV = ptrs(gUs), ptrs(gSs), ptrs(gVs)
+        flags = torch.zeros(b, dtype=torch.int32, device=dev)
+        mpjsvd_set_stream(self.h, torch.cuda.current_stream(dev).cuda_stream)
+        rc = mpjsvd_svd_backward_batched(
+            self.h, b, m.ctypes.data, n.ctypes.data, pU.data_ptr(), pS.data_ptr(), pV.data_ptr(),
+            pgU.data_ptr() if pgU is not None else None, pgS.data_ptr() if pgS is not None else None,
+            pgV.data_ptr() if pgV is not None else None, pA.data_ptr(), gap_tol, flags.data_ptr())
+        _check(rc, "mpjsvd_svd_backward_batched")
+        self._keep_bwd = (keep, pU, pS, pV, pA, pgU, pgS, pgV)  # alive until the next call
+        return gAs, flags
 
     def close(self):
         if self.h:
@@ -336,7 +399,10 @@ def default_handle(device=None):
 
 def svd(A, mode="auto", tol=0.0, **params):
     """Thin SVD through the library. A CPU input is copied to the current GPU and the
-    factors are copied back (end-to-end use); a CUDA input stays on the device."""
+    factors are copied back (end-to-end use); a CUDA input stays on the device. A CUDA input
+    that requires grad goes through SVDFunction (the library's hand-written adjoint)."""
+    if A.is_cuda and A.requires_grad and torch.is_grad_enabled():
+        return SVDFunction.apply(A, mode)
     host = not A.is_cuda
     dev = torch.device("cuda", torch.cuda.current_device())
     Ad = colmajor(A.to(torch.float64), dev) if host else A
@@ -348,8 +414,17 @@ def svd(A, mode="auto", tol=0.0, **params):
     return U, S, V
 
 
+def last_backward_flags(device=None):
+    """Near-degenerate count of the last adjoint computed on the default handle of `device`
+    (pairs with |s_i - s_j| <= gap_tol max(s_i, s_j) plus s_i <= 2^-53 s_0), or None."""
+    h = _default.get(torch.cuda.current_device() if device is None else device)
+    return getattr(h, "last_n_flagged", None) if h is not None else None
+
+
 class SVDFunction(torch.autograd.Function):
-    """A -> (U, S, V) with the library's forward and hand-written adjoint."""
+    """A -> (U, S, V) with the library's forward and hand-written adjoint. Near-degenerate
+    singular values are never clamped: the backward warns with their count, which stays
+    readable afterwards through last_backward_flags() and the handle's stats (n_flagged)."""
 
     @staticmethod
     def forward(ctx, A, mode="auto"):
@@ -364,5 +439,8 @@ class SVDFunction(torch.autograd.Function):
         U, S, V = ctx.saved_tensors
         h = default_handle(U.device.index)
         gA, nf = h.backward(U, S, V, gU, gS, gV)
-        ctx.n_flagged = nf
+        if nf:
+            warnings.warn("mpjsvd adjoint: %d near-degenerate singular value pair(s) or tiny "
+                          "singular value(s); the 1/(s_j^2 - s_i^2) terms are large" % nf,
+                          RuntimeWarning, stacklevel=2)
         return gA, None
