@@ -64,6 +64,12 @@ extern "C" {
                                 default */
 #define MPJSVD_QRCP_F64 1    /* Businger-Golub QR with column pivoting in binary64 */
 
+/* params.low_kernel: the kernel of the binary32 stage (Section 3.2). */
+#define MPJSVD_LOWK_AUTO 0   /* the tensor-core form where it is faster (chosen by size) */
+#define MPJSVD_LOWK_TC 1     /* blocked form on the tensor cores: 64-column blocks, pair Gram
+                                matrices and rotation application by TF32x3 tcgen05 MMAs */
+#define MPJSVD_LOWK_REG 2    /* register-resident level-1 visits (no tensor cores) */
+
 /* params.stop: when Alg. 1 (both precisions) stops. */
 #define MPJSVD_STOP_XGESVJ 0 /* default: after a sweep without rotations, or after a sweep other
                                 than the first whose rotations were all negligible (largest
@@ -94,6 +100,7 @@ typedef struct {
     int wait_limit_ms;    /* 4000: every bounded device wait of a call (a grid barrier, a block
                              hand-off between CTAs) gives up after this many milliseconds and
                              records MPJSVD_STATUS_TIMEOUT; 1 .. 600000 */
+    int low_kernel;       /* MPJSVD_LOWK_* */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
@@ -248,9 +255,19 @@ int mpjsvd_geqp3(mpjsvd_handle h, int m, int n, double* A, int lda, int* jpvt, d
 int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, int lda,
                    const double* tau, double* C, int ldc);
 
+/* The two tensor-core steps of a visit of the blocked binary32 stage (Section 3.2 in blocked
+ * form) as a standalone call, for one block pair Z = [X_I X_J] of 128 columns:
+ *   G = Z^T Z     (if G is not NULL; G: device, 128 x 128 binary32, column-major)
+ *   Z <- Z W      (if W is not NULL, after G; W: device, 128 x 128 binary32, column-major)
+ * both by TF32 tcgen05 MMAs with a 3-term split (hi = tf32(z), lo = tf32(z - hi);
+ * hi hi' + hi lo' + lo hi'), accumulated in binary32.
+ *   m : rows of Z, 1 <= m; Z: device, m x 128 binary32, leading dimension ldz >= m
+ * Stream-ordered on the handle's stream; one CTA. */
+int mpjsvd_tc_block_f32(mpjsvd_handle h, int m, float* Z, int ldz, float* G, const float* W);
+
 /* Measurement utility (not part of the paper): the FP64 FMA throughput of the current GPU in
  * TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on every SM, timed with
- * CUDA events on cuda_stream (best of three launches after a warm-up; about 0.1 s). This is
+ * CUDA events on cuda_stream (best of three launches after a warm-up; about 0.4 s). This is
  * the denominator of the FP64 roofline fractions. Returns 0, -2 for a NULL tflops,
  * MPJSVD_ERR_CUDA. Synchronizes cuda_stream. */
 int mpjsvd_measure_fp64_peak(void* cuda_stream, double* tflops);

@@ -86,6 +86,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->qrcp = MPJSVD_QRCP_MIXED;
     p->stop = MPJSVD_STOP_XGESVJ;
     p->wait_limit_ms = 4000;
+    p->low_kernel = MPJSVD_LOWK_AUTO;
     return 0;
 }
 
@@ -99,6 +100,7 @@ static int check_params(const mpjsvd_params* p)
     if (p->stop < 0 || p->stop > 1) return 1;
     if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
     if (p->wait_limit_ms < 1 || p->wait_limit_ms > 600000) return 1;
+    if (p->low_kernel < 0 || p->low_kernel > 2) return 1;
     return 0;
 }
 

@@ -63,6 +63,11 @@ int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st,
                       int gate_want, int* threads_out);
 int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
                       int phase, int gate_want, int* threads_out);
+// the binary32 stage in blocked form on the tensor cores (bsweep_tc.cu): block width 64
+int launch_bsweeps_tf32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st, int phase,
+                        int gate_want);
+// its building blocks as a standalone call: G = Z^T Z and / or Z <- Z W for a 128-column Z
+int tc_block_call(mpjsvd_ctx* h, int m, float* Z, int ldz, float* G, const float* W);
 // largest block width <= w_want whose register-resident visit holds mX rows (0: none)
 int sweep_fit_w_f32(int mX, int w_want);
 int sweep_fit_w_f64(int mX, int w_want);

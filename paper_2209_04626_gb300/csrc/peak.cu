@@ -10,7 +10,7 @@ namespace mpj {
 // cover the FP64 pipe's latency on every sub-partition). The result is stored only if it is
 // impossible (never in practice), so the compiler keeps every FMA.
 constexpr int kChains = 8;
-constexpr int kIters = 4096;
+constexpr int kIters = 16384;  // about 0.1 s per launch: long enough for the clocks to settle
 
 static __global__ void __launch_bounds__(256) k_fp64_fma(double seed, double* sink)
 {

@@ -24,7 +24,8 @@
 
 namespace mpj {
 
-constexpr int kWmaxLow = 16;   // widest binary32 block
+constexpr int kWmaxLow = 16;   // widest binary32 block (register-resident visits)
+constexpr int kLowTcMinN = 512; // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
 constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
@@ -721,7 +722,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // ---- [3.2] binary32 Jacobi on low(X), U only (gated)
     const size_t nn = (size_t)n * n;
     // the register file bounds the width for tall X: fall back to narrower blocks
-    int w_low = sweep_fit_w_f32(n, pick_w(n, n, true, h->num_sms, P.block_w));
+    // binary32 stage: the blocked tensor-core form (64-column blocks) or register-resident
+    // level-1 visits
+    const bool low_tc = P.low_kernel == MPJSVD_LOWK_TC ||
+                        (P.low_kernel == MPJSVD_LOWK_AUTO && n >= kLowTcMinN);
+    int w_low = low_tc ? 64 : sweep_fit_w_f32(n, pick_w(n, n, true, h->num_sms, P.block_w));
     int w_work = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
     if (w_low == 0 || w_work == 0)
         return cuda_fail("sweeps: no register-resident variant holds n rows", cudaErrorInvalidValue);
@@ -735,7 +740,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         Dl.k = sweep_blocks(n, w_low); Dl.maxsweep = std::min(P.maxsweep, 64); Dl.tol = tol_low;
         Dl.stop = P.stop;
         Dl.dsc = dsc; Dl.alph = alph; Dl.ver = ver;
-        if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
+        if (low_tc) {
+            if ((rc = launch_bsweeps_tf32(h, Dl, Xl, st, 0, 1))) return rc;
+        } else {
+            if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
+        }
         k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
         k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
         k_make_ul<<<std::min(n, egrid), T256, 0, s>>>(n, Xl, sigl, ord, Ul, st); ++h->launch_count;

@@ -21,6 +21,7 @@ MODE = {"auto": 0, "mixed": 1, "plain": 2}
 PRECOND = {"rt": 0, "r": 1}
 QRCP = {"mixed": 0, "f64": 1}
 STOP = {"xgesvj": 0, "alg1": 1}
+LOWK = {"auto": 0, "tc": 1, "reg": 2}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -28,7 +29,7 @@ EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsv
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
            "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
            "mpjsvd_apply_q", "mpjsvd_geqp3", "mpjsvd_selftest_timeout",
-           "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak"]
+           "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak", "mpjsvd_tc_block_f32"]
 
 
 class Params(ctypes.Structure):
@@ -36,7 +37,8 @@ class Params(ctypes.Structure):
                 ("tol_cond_coef", ctypes.c_double), ("trailing_frac", ctypes.c_double),
                 ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
-                ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int)]
+                ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
+                ("low_kernel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +90,7 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_geqp3.argtypes = [_vp, _i, _i, _vp, _i, _vp, _vp]
     L.mpjsvd_selftest_timeout.argtypes = [_vp]
     L.mpjsvd_measure_fp64_peak.argtypes = [_vp, ctypes.POINTER(_d)]
+    L.mpjsvd_tc_block_f32.argtypes = [_vp, _i, _vp, _i, _vp, _vp]
     L.mpjsvd_svd_backward_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _d, _vp]
     _lib = L
@@ -114,6 +117,8 @@ def mpjsvd_default_params(**overrides):
             v = QRCP[v]
         if k == "stop" and isinstance(v, str):
             v = STOP[v]
+        if k == "low_kernel" and isinstance(v, str):
+            v = LOWK[v]
         setattr(p, k, v)
     return p
 
@@ -191,6 +196,10 @@ def mpjsvd_measure_fp64_peak(stream=None):
     return v.value
 
 
+def mpjsvd_tc_block_f32(h, m, Z_ptr, ldz, G_ptr, W_ptr):
+    return load_library().mpjsvd_tc_block_f32(h, m, _vp(Z_ptr), ldz, _vp(G_ptr), _vp(W_ptr))
+
+
 def mpjsvd_selftest_timeout(h):
     return load_library().mpjsvd_selftest_timeout(h)
 
@@ -243,6 +252,8 @@ class Handle:
                 v = QRCP[v]
             if k == "stop" and isinstance(v, str):
                 v = STOP[v]
+            if k == "low_kernel" and isinstance(v, str):
+                v = LOWK[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 

@@ -138,11 +138,17 @@ def test_batched_adjoint_differentiation_workload():
         A, _, w, GU, GV = items[b]
         E = rng.standard_normal(A.shape)
 
+        Vref = Vs[b]
+
         def loss(X):
+            # the sign rule (largest |v_ik| positive) is discontinuous where two entries tie in
+            # magnitude; the derivative is that of the branch through A, so the perturbed
+            # factors are oriented like A's before the loss is taken
             U, S, V, _ = h.svd_batched([mpjsvd.colmajor(torch.from_numpy(X), dev)])
+            sg = torch.sign((V[0] * Vref).sum(0))
             return float((torch.from_numpy(w).to(dev) * S[0]).sum() +
-                         (torch.from_numpy(GU).to(dev) * U[0]).sum() +
-                         (torch.from_numpy(GV).to(dev) * V[0]).sum())
+                         (torch.from_numpy(GU).to(dev) * (U[0] * sg)).sum() +
+                         (torch.from_numpy(GV).to(dev) * (V[0] * sg)).sum())
         fd = [(loss(A + s * E) - loss(A - s * E)) / (2 * s) for s in (hstep, 2 * hstep)]
         an = float(np.sum(gAs[b].cpu().numpy() * E))
         trunc = abs(fd[1] - fd[0]) / 3.0
