@@ -38,19 +38,27 @@ constexpr int kBW = 64;         // block width
 constexpr int kB2 = 128;        // columns of a visit
 constexpr int kBThreads = 256;
 constexpr int kGP = 129;        // padded row stride (floats) of G and W in shared memory
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 256;   // two 128-column FP32 accumulators
 constexpr uint32_t kIdescTF32 = tc_idesc(128, 128, kTcFmtTF32);
 
-// dynamic shared memory: three regions
-constexpr size_t kRegStage = 65536;                      // Gram chunk staging; apply buffer 1
-constexpr size_t kRegG = 66560;                          // G; later the B tiles of W (hi, lo)
-constexpr size_t kRegW = 66560;                          // W; later apply buffer 0
-constexpr size_t kBSmem = kRegStage + kRegG + kRegW;     // 198656 bytes
+// dynamic shared memory, three regions:
+//   [0, 64 KiB)          Gram: two chunk buffers (hi 16 KiB + lo 16 KiB each)
+//   [64 KiB, +kRegG)     G (128 x kGP floats)
+//   [.., +kRegW)         W (128 x kGP floats)
+// during the application of W, the B tiles of W (hi and lo, 64 KiB each) take [0, 128 KiB)
+// (the Gram buffers and the dead G) and the A tiles of a 128-row chunk half (hi and lo,
+// 32 KiB each) take W's region once W has been split
+constexpr size_t kRegStage = 65536;
+constexpr size_t kRegG = 66560;
+constexpr size_t kRegW = 66560;
+constexpr size_t kRegTab = 8192;                         // pairs of the intra rounds
+constexpr size_t kBSmem = kRegStage + kRegG + kRegW + kRegTab;  // 206848 bytes
 
 struct BVisitShared {
     int gidx[kB2];
     float cs[kBW], sn[kBW], nal[kBW], nbe[kBW];
     unsigned act[2];          // active pairs of the current inner round (bits 0..63)
+    unsigned char pa[kBW], pb[kBW];  // the pairs of the current inner round
     int nrot;
     unsigned mxc, mxt;        // binary32 bits: largest cosine and |tan| rotated in the visit
     uint64_t mbar[2];
@@ -72,9 +80,11 @@ __device__ __forceinline__ void bpair(bool intra, int q, int p, int& a, int& b)
     b += base;
 }
 
-// Wait (bounded) for every commit issued on mbarrier i that has not been waited for.
+// Wait (bounded) for every commit issued on mbarrier i that has not been waited for. Starts
+// with a CTA barrier, so every thread sees the count that thread 0 (the MMA issuer) left.
 __device__ __forceinline__ bool drain(BVisitShared& s, int i, DevState* st)
 {
+    __syncthreads();
     while (s.pend[i]) {
         if (!mbar_wait(&s.mbar[i], s.par[i], st)) return false;
         __syncthreads();
@@ -87,33 +97,45 @@ __device__ __forceinline__ bool drain(BVisitShared& s, int i, DevState* st)
     return true;
 }
 
+// Loads of the Gram step for one chunk of kGramKC = 32 rows: 16 groups of 8 columns, two per
+// warp; lane: column 8 cg + (lane & 7), rows 8 (lane >> 3) .. + 7 of the chunk.
+__device__ __forceinline__ void gram_load(const float* X, int ldX, int mX, const BVisitShared& s, int ch,
+                                          float (&v)[2][8])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int c = (warp + 8 * rep) * 8 + (lane & 7);
+        const int gc = s.gidx[c];
+        const int row0 = ch * 32 + 8 * (lane >> 3);
+        const float* col = X + (size_t)(gc < 0 ? 0 : gc) * ldX;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = row0 + i;
+            v[rep][i] = (gc >= 0 && r < mX) ? __ldcg(col + r) : 0.0f;
+        }
+    }
+}
+
 // 1. G = Z^T Z into shared memory (row stride kGP); Z = columns gidx[] of X, rows 0..mX-1.
-// Returns false if a wait gave up.
+// The loads of chunk ch + 1 are issued while the MMAs of chunk ch run. Returns false if a
+// wait gave up.
 __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsigned char* dsm,
                           float* G, DevState* st)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nch = (mX + 31) / 32;
+    float v[2][8];
+    gram_load(X, ldX, mX, s, 0, v);
     for (int ch = 0; ch < nch; ++ch) {
         const int buf = ch & 1;
         if (!drain(s, buf, st)) return false;  // MMAs of chunk ch - 2 have read the buffer
-        float* hi = (float*)(dsm + buf * 32768);
-        float* lo = (float*)(dsm + buf * 32768 + 16384);
-        // 16 groups of 8 columns, two per warp; lane: column 8 cg + (lane & 7), rows
-        // 8 (lane >> 3) .. + 7 of the chunk; stored as two 16-byte pieces (core matrices k4 =
-        // 2 (lane >> 3) and + 1 of row group cg)
+        unsigned char* hi = dsm + buf * 32768;
+        unsigned char* lo = hi + 16384;
+        // two 16-byte pieces per group: core matrices k4 = 2 (lane >> 3) and + 1 of row group cg
 #pragma unroll
         for (int rep = 0; rep < 2; ++rep) {
-            const int cg = warp + 8 * rep;
-            const int c = cg * 8 + (lane & 7), rg = lane >> 3;
-            const int gc = s.gidx[c];
-            const int row0 = ch * 32 + 8 * rg;
-            float v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = row0 + i;
-                v[i] = (gc >= 0 && r < mX) ? __ldcg(X + (size_t)gc * ldX + r) : 0.0f;
-            }
+            const int cg = warp + 8 * rep, c = cg * 8 + (lane & 7), rg = lane >> 3;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 float4 h4, l4;
@@ -121,14 +143,14 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
                 float* lp = &l4.x;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float x = v[4 * q + e];
+                    const float x = v[rep][4 * q + e];
                     const float hx = tf32_rna(x);
                     hp[e] = hx;
                     lp[e] = tf32_rna(x - hx);
                 }
                 const size_t off = (size_t)cg * 1024 + (size_t)(2 * rg + q) * 128 + (size_t)(c & 7) * 16;
-                *(float4*)((unsigned char*)hi + off) = h4;
-                *(float4*)((unsigned char*)lo + off) = l4;
+                *(float4*)(hi + off) = h4;
+                *(float4*)(lo + off) = l4;
             }
         }
         fence_async_smem();
@@ -137,8 +159,8 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ah = tc_desc((unsigned char*)hi + ks * 256, 128, 1024);
-                const uint64_t al = tc_desc((unsigned char*)lo + ks * 256, 128, 1024);
+                const uint64_t ah = tc_desc(hi + ks * 256, 128, 1024);
+                const uint64_t al = tc_desc(lo + ks * 256, 128, 1024);
                 tc_mma_tf32(s.tmem, ah, ah, kIdescTF32, (ch > 0 || ks > 0) ? 1u : 0u);
                 tc_mma_tf32(s.tmem, ah, al, kIdescTF32, 1u);
                 tc_mma_tf32(s.tmem, al, ah, kIdescTF32, 1u);
@@ -146,7 +168,7 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             tc_commit(&s.mbar[buf]);
             ++s.pend[buf];
         }
-        __syncthreads();
+        if (ch + 1 < nch) gram_load(X, ldX, mX, s, ch + 1, v);
     }
     if (!drain(s, 0, st) || !drain(s, 1, st)) return false;
     // read back: warp w holds lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
@@ -154,23 +176,86 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
     const int row = base + lane;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float v[16];
-        tmem_ld16(s.tmem + ((uint32_t)base << 16) + (uint32_t)(c0 + 16 * q), v);
+        float x[16];
+        tmem_ld16(s.tmem + ((uint32_t)base << 16) + (uint32_t)(c0 + 16 * q), x);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) G[row * kGP + c0 + 16 * q + e] = v[e];
+        for (int e = 0; e < 16; ++e) G[row * kGP + c0 + 16 * q + e] = x[e];
     }
     tc_fence_before();
     __syncthreads();
     return true;
 }
 
+// Loads of one half (64 of the 128 columns) of a 128-row chunk for the application of W:
+// thread: rows i = tid & 127, columns 4 k4 .. + 3 for k4 = tid >> 7, + 2, ..., + 14.
+__device__ __forceinline__ void apply_load(const float* X, int ldX, int mX, const BVisitShared& s, int r0,
+                                           int hlf, float (&v)[8][4])
+{
+    const int i = threadIdx.x & 127, k0 = threadIdx.x >> 7;
+    const int r = r0 + i;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int k4 = k0 + 2 * t;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gc = s.gidx[64 * hlf + 4 * k4 + j];
+            v[t][j] = (gc >= 0 && r < mX) ? __ldcg(X + (size_t)gc * ldX + r) : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ void apply_store_a(unsigned char* ahi, unsigned char* alo, const float (&v)[8][4])
+{
+    const int i = threadIdx.x & 127, k0 = threadIdx.x >> 7;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int k4 = k0 + 2 * t;
+        float4 h4, l4;
+        float* hp = &h4.x;
+        float* lp = &l4.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float hx = tf32_rna(v[t][j]);
+            hp[j] = hx;
+            lp[j] = tf32_rna(v[t][j] - hx);
+        }
+        const size_t off = (size_t)(i >> 3) * 2048 + (size_t)k4 * 128 + (size_t)(i & 7) * 16;
+        *(float4*)(ahi + off) = h4;
+        *(float4*)(alo + off) = l4;
+    }
+}
+
+// Epilogue of a chunk: accumulator columns (tensor memory at acc) -> rows r0.. of Z.
+__device__ __forceinline__ void apply_epilogue(float* X, int ldX, int mX, const BVisitShared& s, int r0,
+                                               uint32_t acc)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = 32 * (warp & 3), c0 = 64 * (warp >> 2);
+    const int r = r0 + base + lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float x[16];
+        tmem_ld16(acc + ((uint32_t)base << 16) + (uint32_t)(c0 + 16 * q), x);
+        if (r < mX) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int gc = s.gidx[c0 + 16 * q + e];
+                if (gc >= 0) X[(size_t)gc * ldX + r] = x[e];
+            }
+        }
+    }
+}
+
 // 3. Z <- Z W (columns gidx[] of X, rows 0..mX-1) with W (row stride kGP) in shared memory.
+// Per 128-row chunk c: the two column halves of A go through one shared buffer; the chunk's
+// MMAs accumulate into tensor-memory columns 128 (c & 1) .. + 127, so the epilogue of chunk
+// c - 1 and the loads of the next half run while the tensor core works.
 __device__ bool apply_tf32(float* X, int ldX, int mX, BVisitShared& s, unsigned char* dsm,
                            const float* W, DevState* st)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned char* bhi = dsm + kRegStage;                 // over G (dead after the rotations)
-    unsigned char* blo = dsm + kRegStage + 32768;
+    const int tid = threadIdx.x;
+    unsigned char* bhi = dsm;                             // over the Gram buffers and G
+    unsigned char* blo = dsm + 65536;
     // B (N x K) = W^T, K-major: row n, reduction index k: B(n, k) = W(k, n)
     for (int e = tid; e < kB2 * 32; e += kBThreads) {
         const int n = e & 127, k4 = e >> 7;
@@ -188,34 +273,18 @@ __device__ bool apply_tf32(float* X, int ldX, int mX, BVisitShared& s, unsigned 
         *(float4*)(bhi + off) = h4;
         *(float4*)(blo + off) = l4;
     }
-    __syncthreads();  // W is read: its region becomes apply buffer 0
+    __syncthreads();  // W is read: its region holds the A tiles from here on
+    unsigned char* ahi = dsm + kRegStage + kRegG;
+    unsigned char* alo = ahi + 32768;
     const int nch = (mX + 127) / 128;
+    float v[8][4];
+    apply_load(X, ldX, mX, s, 0, 0, v);
     for (int ch = 0; ch < nch; ++ch) {
         const int r0 = ch * 128;
+        const uint32_t acc = s.tmem + 128u * (uint32_t)(ch & 1);
         for (int hlf = 0; hlf < 2; ++hlf) {
-            if (!drain(s, hlf, st)) return false;
-            unsigned char* abuf = (hlf == 0) ? dsm + kRegStage + kRegG : dsm;
-            unsigned char* ahi = abuf;
-            unsigned char* alo = abuf + 32768;
-            // A (M x K) = rows r0.. of Z, columns 64 hlf .. + 63; thread: row i, 4 columns
-            for (int e = tid; e < 128 * 16; e += kBThreads) {
-                const int i = e & 127, k4 = e >> 7;
-                const int r = r0 + i;
-                float4 h4, l4;
-                float* hp = &h4.x;
-                float* lp = &l4.x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int gc = s.gidx[64 * hlf + 4 * k4 + j];
-                    const float x = (gc >= 0 && r < mX) ? __ldcg(X + (size_t)gc * ldX + r) : 0.0f;
-                    const float hx = tf32_rna(x);
-                    hp[j] = hx;
-                    lp[j] = tf32_rna(x - hx);
-                }
-                const size_t off = (size_t)(i >> 3) * 2048 + (size_t)k4 * 128 + (size_t)(i & 7) * 16;
-                *(float4*)(ahi + off) = h4;
-                *(float4*)(alo + off) = l4;
-            }
+            if (!drain(s, 0, st)) return false;  // every MMA issued so far is complete
+            apply_store_a(ahi, alo, v);
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -226,39 +295,47 @@ __device__ bool apply_tf32(float* X, int ldX, int mX, BVisitShared& s, unsigned 
                     const uint64_t al = tc_desc(alo + ks * 256, 128, 2048);
                     const uint64_t bh = tc_desc(bhi + (8 * hlf + ks) * 256, 128, 4096);
                     const uint64_t bl = tc_desc(blo + (8 * hlf + ks) * 256, 128, 4096);
-                    tc_mma_tf32(s.tmem, ah, bh, kIdescTF32, (hlf > 0 || ks > 0) ? 1u : 0u);
-                    tc_mma_tf32(s.tmem, ah, bl, kIdescTF32, 1u);
-                    tc_mma_tf32(s.tmem, al, bh, kIdescTF32, 1u);
+                    tc_mma_tf32(acc, ah, bh, kIdescTF32, (hlf > 0 || ks > 0) ? 1u : 0u);
+                    tc_mma_tf32(acc, ah, bl, kIdescTF32, 1u);
+                    tc_mma_tf32(acc, al, bh, kIdescTF32, 1u);
                 }
-                tc_commit(&s.mbar[hlf]);
-                ++s.pend[hlf];
+                tc_commit(&s.mbar[0]);
+                ++s.pend[0];
             }
-            __syncthreads();
-        }
-        if (!drain(s, 0, st) || !drain(s, 1, st)) return false;
-        // epilogue: row base + lane of the chunk, columns c0 .. c0 + 63
-        const int base = 32 * (warp & 3), c0 = 64 * (warp >> 2);
-        const int r = r0 + base + lane;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float v[16];
-            tmem_ld16(s.tmem + ((uint32_t)base << 16) + (uint32_t)(c0 + 16 * q), v);
-            if (r < mX) {
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int gc = s.gidx[c0 + 16 * q + e];
-                    if (gc >= 0) X[(size_t)gc * ldX + r] = v[e];
-                }
+            // the next half's (or chunk's) loads, then (after the first half) the previous
+            // chunk's epilogue, while the MMAs run; its accumulator's MMAs completed before
+            // this half was stored (drain above)
+            if (hlf == 0) apply_load(X, ldX, mX, s, r0, 1, v);
+            else if (ch + 1 < nch) apply_load(X, ldX, mX, s, r0 + 128, 0, v);
+            if (hlf == 0 && ch > 0) {
+                apply_epilogue(X, ldX, mX, s, r0 - 128, s.tmem + 128u * (uint32_t)((ch - 1) & 1));
+                tc_fence_before();
             }
         }
-        tc_fence_before();
-        __syncthreads();
     }
+    if (!drain(s, 0, st)) return false;
+    apply_epilogue(X, ldX, mX, s, (nch - 1) * 128, s.tmem + 128u * (uint32_t)((nch - 1) & 1));
+    tc_fence_before();
+    __syncthreads();
     return true;
 }
 
+// Pair tables of the inner rounds of a 64-column block pair (columns 0..63 = I, 64..127 = J):
+// cross round q pairs (p, 64 + (p + q) % 64); intra round q (first round of a sweep) pairs the
+// columns inside I and inside J by the round-robin of rr_pair, 32 pairs each.
+__device__ __forceinline__ void intra_table(unsigned short* tab)
+{
+    for (int e = threadIdx.x; e < (kBW - 1) * kBW; e += blockDim.x) {
+        const int q = e / kBW, p = e % kBW;
+        int a, b;
+        bpair(true, q, p, a, b);
+        tab[e] = (unsigned short)(a | (b << 8));
+    }
+}
+
 // 2. the visit's inner rounds on G, accumulating W. Returns the number of rotations.
-__device__ int rotate_gram(float* G, float* W, bool first, float tol, BVisitShared& s)
+__device__ int rotate_gram(float* G, float* W, bool first, float tol, BVisitShared& s,
+                           const unsigned short* itab)
 {
     const int tid = threadIdx.x;
     for (int e = tid; e < kB2 * kB2; e += kBThreads) {
@@ -274,7 +351,16 @@ __device__ int rotate_gram(float* G, float* W, bool first, float tol, BVisitShar
         // rotation parameters: thread p < 64 for pair p
         if (tid < kBW) {
             int a, b;
-            bpair(intra, q, tid, a, b);
+            if (intra) {
+                const unsigned short ab = itab[q * kBW + tid];
+                a = ab & 0xff;
+                b = ab >> 8;
+            } else {
+                a = tid;
+                b = kBW + ((tid + q) & (kBW - 1));
+            }
+            s.pa[tid] = (unsigned char)a;
+            s.pb[tid] = (unsigned char)b;
             bool act = false;
             float cs = 0.0f, ta = 0.0f;
             if (s.gidx[a] >= 0 && s.gidx[b] >= 0) {
@@ -304,14 +390,14 @@ __device__ int rotate_gram(float* G, float* W, bool first, float tol, BVisitShar
         __syncthreads();
         const unsigned m0 = s.act[0], m1 = s.act[1];
         if ((m0 | m1) == 0u) continue;  // uniform: every thread read the same masks
-        // G <- J^T G (rows a, b of every active pair); thread: column j, pairs of one parity
+        const int half = tid >> 7;                       // pairs 0..31 or 32..63
+        unsigned mk = half ? m1 : m0;
+        // G <- J^T G (rows a, b of every active pair); thread: column j
         {
-            const int j = tid & 127, par = tid >> 7;
-            for (int p = par; p < kBW; p += 2) {
-                const unsigned mk = (p < 32) ? m0 : m1;
-                if (!(mk & (1u << (p & 31)))) continue;
-                int a, b;
-                bpair(intra, q, p, a, b);
+            const int j = tid & 127;
+            for (unsigned m = mk; m; m &= m - 1) {
+                const int p = 32 * half + __ffs(m) - 1;
+                const int a = s.pa[p], b = s.pb[p];
                 const float c = s.cs[p], sv = s.sn[p];
                 const float ga = G[a * kGP + j], gb = G[b * kGP + j];
                 G[a * kGP + j] = fmaf(c, ga, -sv * gb);
@@ -320,14 +406,12 @@ __device__ int rotate_gram(float* G, float* W, bool first, float tol, BVisitShar
         }
         __syncthreads();
         // G <- G J and W <- W J (columns a, b); the 2 x 2 block of each pair gets its exact
-        // result (alpha - t gamma, beta + t gamma, 0); thread: row i, pairs of one parity
+        // result (alpha - t gamma, beta + t gamma, 0); thread: row i
         {
-            const int i = tid & 127, par = tid >> 7;
-            for (int p = par; p < kBW; p += 2) {
-                const unsigned mk = (p < 32) ? m0 : m1;
-                if (!(mk & (1u << (p & 31)))) continue;
-                int a, b;
-                bpair(intra, q, p, a, b);
+            const int i = tid & 127;
+            for (unsigned m = mk; m; m &= m - 1) {
+                const int p = 32 * half + __ffs(m) - 1;
+                const int a = s.pa[p], b = s.pb[p];
                 const float c = s.cs[p], sv = s.sn[p];
                 const float ga = G[i * kGP + a], gb = G[i * kGP + b];
                 float na = fmaf(c, ga, -sv * gb), nb = fmaf(sv, ga, c * gb);
@@ -359,7 +443,8 @@ __device__ int bvisit(const SweepDims& D, float* X, int bi, int bj, bool first, 
     float* G = (float*)(dsm + kRegStage);
     float* W = (float*)(dsm + kRegStage + kRegG);
     if (!gram_tf32(X, D.ldX, D.mX, s, dsm, G, st)) return -1;
-    const int nrot = rotate_gram(G, W, first, (float)D.tol, s);
+    const int nrot = rotate_gram(G, W, first, (float)D.tol, s,
+                                 (const unsigned short*)(dsm + kRegStage + kRegG + kRegW));
     if (nrot > 0 && !apply_tf32(X, D.ldX, D.mX, s, dsm, W, st)) return -1;
     return nrot;
 }
@@ -425,6 +510,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_bsweeps_tf32(SweepDims D, floa
     __syncthreads();
     tc_fence_after();
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.k; b += gridDim.x * blockDim.x) D.ver[b] = 0u;
+    intra_table((unsigned short*)(dsm + kRegStage + kRegG + kRegW));
     int sweeps = -1;
     bool conv = false;
     if (g.sync())

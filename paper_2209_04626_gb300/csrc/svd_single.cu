@@ -25,7 +25,7 @@
 namespace mpj {
 
 constexpr int kWmaxLow = 16;   // widest binary32 block (register-resident visits)
-constexpr int kLowTcMinN = 512; // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
+constexpr int kLowTcMinN = 4096;  // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
 constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch

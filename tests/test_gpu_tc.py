@@ -22,7 +22,8 @@ def _block(Z, W=None, gram=True):
     m = Z.shape[0]
     Zd = torch.from_numpy(np.asfortranarray(Z, dtype=np.float32).T.copy()).to(dev).t()  # column-major
     G = torch.zeros((128, 128), dtype=torch.float32, device=dev) if gram else None
-    Wd = torch.from_numpy(np.asfortranarray(W, dtype=np.float32).T.copy()).to(dev).t().contiguous().t() \
+    # W column-major: the row-major buffer of W^T
+    Wd = torch.from_numpy(np.ascontiguousarray(np.asarray(W, dtype=np.float32).T)).to(dev) \
         if W is not None else None
     h = mpjsvd.Handle()
     rc = mpjsvd.mpjsvd_tc_block_f32(h.h, m, Zd.data_ptr(), m, G.data_ptr() if gram else None,
