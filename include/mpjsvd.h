@@ -58,6 +58,11 @@ extern "C" {
 
 #define MPJSVD_PRECOND_RT 0  /* Jacobi on X = R^T (lower triangular); default */
 #define MPJSVD_PRECOND_R 1   /* Jacobi on X = R (Alg. 4 with Q2 = I) */
+#define MPJSVD_PRECOND_L 2   /* Jacobi on X = L from the second preconditioning R = L Q2^T
+                                (the LQ of R as the QR of R^T; Alg. 2, Section 2.2) */
+#define MPJSVD_PRECOND_AUTO 3 /* Alg. 2's choice: X = R when R is "almost diagonal" (every
+                                column diagonally dominant, |r_jj| >= sum_{i<j} |r_ij|), else
+                                X = L; decided on the device (single-matrix path only) */
 
 /* params.qrcp: the rank-revealing QR of the preconditioning (Section 3.1). */
 #define MPJSVD_QRCP_MIXED 0  /* Alg. 5: binary32 pivot search on lower(A), binary64 QR of A P;
@@ -69,6 +74,13 @@ extern "C" {
 #define MPJSVD_LOWK_TC 1     /* blocked form on the tensor cores: 64-column blocks, pair Gram
                                 matrices and rotation application by TF32x3 tcgen05 MMAs */
 #define MPJSVD_LOWK_REG 2    /* register-resident level-1 visits (no tensor cores) */
+
+/* params.switch_method: the precision switch of Section 3.3. */
+#define MPJSVD_SWITCH_U 0    /* B = X^T U_low, B = Q R2, Y = X Q (the method the paper prefers;
+                                default) */
+#define MPJSVD_SWITCH_V 1    /* the alternative: the binary32 stage also accumulates V_low
+                                (its rotations applied in binary64), V_low = Q R2, Y = X Q;
+                                runs the register-resident binary32 stage */
 
 /* params.stop: when Alg. 1 (both precisions) stops. */
 #define MPJSVD_STOP_XGESVJ 0 /* default: after a sweep without rotations, or after a sweep other
@@ -101,6 +113,14 @@ typedef struct {
                              hand-off between CTAs) gives up after this many milliseconds and
                              records MPJSVD_STATUS_TIMEOUT; 1 .. 600000 */
     int low_kernel;       /* MPJSVD_LOWK_* */
+    int v_by_qr;          /* 1: the refinement runs without V, then V comes from the QR of
+                             X^T U_X and one more Alg. 1 with V accumulated from that Q
+                             (Section 3.4); 0 (default): V accumulated through the refinement */
+    int switch_method;    /* MPJSVD_SWITCH_* */
+    double y_tol;         /* > 0: the Y1/Y2 safeguard of Section 3.4 with this cosine
+                             threshold (Y2 = the columns of Y from the first one whose largest
+                             cosine with an earlier column exceeds y_tol: Alg. 1 on Y2, one pass
+                             over the Y1 x Y2 pairs, then the refinement); 0 (default): off */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
@@ -124,6 +144,12 @@ typedef struct {
     float ms_final;
     int launches;         /* CUDA kernels the call launched (gated-off stages included) */
     int qrcp;             /* the RRQR that ran: MPJSVD_QRCP_MIXED or MPJSVD_QRCP_F64 */
+    int precond;          /* the Jacobi input that ran: MPJSVD_PRECOND_RT, _R or _L */
+    int sweeps_v;         /* binary64 sweeps outside the refinement proper: the safeguard's
+                             Alg. 1 on Y2 and its pass over Y1 x Y2, the final Alg. 1 with V of
+                             params.v_by_qr */
+    long long rot_v;      /* rotations of those sweeps */
+    int y2_cols;          /* columns the safeguard put in Y2 (0: inactive or off) */
     int n_flagged;        /* near-degenerate count of the handle's last mpjsvd_svd_backward
                              (pairs with |s_i - s_j| <= gap_tol max(s_i, s_j) plus s_i <= 2^-53 s_0);
                              -1 if the handle has run none */

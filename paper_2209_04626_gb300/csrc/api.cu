@@ -87,6 +87,9 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->stop = MPJSVD_STOP_XGESVJ;
     p->wait_limit_ms = 4000;
     p->low_kernel = MPJSVD_LOWK_AUTO;
+    p->v_by_qr = 0;
+    p->switch_method = MPJSVD_SWITCH_U;
+    p->y_tol = 0.0;
     return 0;
 }
 
@@ -95,12 +98,15 @@ static int check_params(const mpjsvd_params* p)
     if (p->maxsweep < 1 || p->maxsweep > 64) return 1;
     if (p->block_w < 0 || p->block_w > 16) return 1;
     if (p->mode < 0 || p->mode > 2) return 1;
-    if (p->precond < 0 || p->precond > 1) return 1;
+    if (p->precond < 0 || p->precond > 3) return 1;
     if (p->qrcp < 0 || p->qrcp > 1) return 1;
     if (p->stop < 0 || p->stop > 1) return 1;
     if (!(p->trailing_frac >= 0.0 && p->trailing_frac <= 1.0)) return 1;
     if (p->wait_limit_ms < 1 || p->wait_limit_ms > 600000) return 1;
     if (p->low_kernel < 0 || p->low_kernel > 2) return 1;
+    if (p->v_by_qr < 0 || p->v_by_qr > 1) return 1;
+    if (p->switch_method < 0 || p->switch_method > 1) return 1;
+    if (!(p->y_tol >= 0.0 && p->y_tol < 1.0)) return 1;
     return 0;
 }
 
@@ -219,6 +225,11 @@ int mpjsvd_svd_batched(mpjsvd_handle h, int batch, const int* m, const int* n, c
     if (!V) return -9;
     if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -10;
     if (!info) return -11;
+    if (h->params.precond > MPJSVD_PRECOND_R) {
+        set_last_error("mpjsvd_svd_batched: params.precond L and AUTO are single-matrix only",
+                       cudaErrorInvalidValue);
+        return -1;
+    }
     return svd_batched(h, batch, m, n, lda, A, U, S, V, tol, info);
 }
 

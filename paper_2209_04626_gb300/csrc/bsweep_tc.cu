@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_bsweeps_tf32(SweepDims D, floa
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ BVisitShared s;
     if (call_failed(st)) return;
-    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
+    if (!gate_open(st, gate_want)) return;
     const Group g{(int)blockIdx.x, (int)gridDim.x, st};
     if (threadIdx.x < 32) tmem_alloc(&s.tmem, kTmemCols);
     if (threadIdx.x == 0) {

@@ -40,13 +40,19 @@ struct DevState {
     double cond_r;
     double orth;
     double maxnorm;        // max column norm of X (branch test)
-    unsigned long long rot_sweep[2][64];   // rotations per sweep, [phase][sweep]
+    unsigned long long rot_sweep[3][64];   // rotations per sweep, [phase][sweep]
     double2 cand[512];                     // QRCP: per-CTA candidate (norm, column) x parity
     unsigned long long amax_bits;          // Alg. 5: max |a_ij| (bits of a non-negative double)
     unsigned long long cand_rec[512];      // Alg. 5: per-CTA step records (tag, column, norm) x parity
-    unsigned mx_cos[2][64];                // binary32 bits: largest cosine among the rotated pairs, [phase][sweep]
-    unsigned mx_tan[2][64];                // binary32 bits: largest |tan| of the rotations, [phase][sweep]
+    unsigned mx_cos[3][64];                // binary32 bits: largest cosine among the rotated pairs, [phase][sweep]
+    unsigned mx_tan[3][64];                // binary32 bits: largest |tan| of the rotations, [phase][sweep]
     unsigned long long spin_ns;            // limit of every bounded wait of the call (0: kSpinLimitNs)
+    int gate_lq;                           // 1: the Jacobi input is X = L (second preconditioning)
+    int gate_y2;                           // 1: the Y1/Y2 safeguard found columns to treat first
+    int y_j0;                              // first column of Y2 (n: none)
+    int y2_cols_n;                         // n of the safeguard's partition
+    int sweeps_v;                          // phase 2 (safeguard passes, final pass of V from QR)
+    unsigned long long rot_v;
 };
 
 // The call's wait limit in nanoseconds.
@@ -54,6 +60,20 @@ __device__ __forceinline__ uint64_t spin_limit_ns(const DevState* st)
 {
     const uint64_t v = *(volatile const unsigned long long*)&st->spin_ns;
     return v ? v : kSpinLimitNs;
+}
+
+// Gates of stages whose execution is decided on the device. gate_want: -1 always; 0 / 1 run
+// only when gate_low (the lower-precision stage of Alg. 4) has that value; kGateLq + 0 / 1: by
+// gate_lq (the second preconditioning of Alg. 2); kGateY2 + 0 / 1: by gate_y2 (the Y1/Y2
+// safeguard).
+constexpr int kGateLq = 2;
+constexpr int kGateY2 = 4;
+__device__ __forceinline__ bool gate_open(const DevState* st, int gate_want)
+{
+    if (gate_want < 0) return true;
+    if (gate_want >= kGateY2) return *(volatile const int*)&st->gate_y2 == gate_want - kGateY2;
+    if (gate_want >= kGateLq) return *(volatile const int*)&st->gate_lq == gate_want - kGateLq;
+    return *(volatile const int*)&st->gate_low == gate_want;
 }
 
 // True once the call cannot produce meaningful output: a non-finite input, or a cooperative

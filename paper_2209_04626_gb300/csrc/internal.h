@@ -31,6 +31,7 @@ struct mpjsvd_ctx {
     int last_block_w_low, last_block_w_work;
     int launch_count;  // kernels launched by the last call
     int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
+    int last_precond;  // MPJSVD_PRECOND_* of the last call (AUTO resolved from the device)
     int* last_flag_dev;  // device count of near-degenerate flags of the last svd_backward
     // the blocked QR's look-ahead: the critical chain (panels and the updates of the next
     // panel) on a high-priority stream, the wide trailing updates on a low-priority one;
@@ -63,6 +64,8 @@ int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st,
                       int gate_want, int* threads_out);
 int launch_sweeps_f64(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st,
                       int phase, int gate_want, int* threads_out);
+int launch_sweeps_f32v(mpjsvd_ctx* h, const SweepDims& D, float* X, double* V, DevState* st, int phase,
+                       int gate_want);
 // the binary32 stage in blocked form on the tensor cores (bsweep_tc.cu): block width 64
 int launch_bsweeps_tf32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st, int phase,
                         int gate_want);

@@ -48,8 +48,7 @@ constexpr size_t kPanelSmemMax = 200 * 1024;
 
 __device__ __forceinline__ bool gate_skip(const DevState* st, int gate_want)
 {
-    if (call_failed(st)) return true;
-    return gate_want >= 0 && *(volatile const int*)&st->gate_low != gate_want;
+    return call_failed(st) || !gate_open(st, gate_want);
 }
 
 // v_k(r) of the panel starting at column j0: 0 above row j0 + k, 1 on it, the stored tail below.

@@ -25,7 +25,7 @@
 namespace mpj {
 
 constexpr int kWmaxLow = 16;   // widest binary32 block (register-resident visits)
-constexpr int kLowTcMinN = 4096;  // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
+constexpr int kLowTcMinN = 5120;  // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
 constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
@@ -83,17 +83,54 @@ __global__ void k_gather_cols(int m, int n, const double* __restrict__ W, int ld
     }
 }
 
-// X = R^T (precond 0) or R (precond 1) from the upper triangle of L (n x n part).
-__global__ void k_form_x(int n, const double* __restrict__ L, int ldl, double* X, int precond)
+// The Jacobi input X from the upper triangle R of L (n x n part): X = R^T (precond RT), X = R
+// (precond R), or, for precond L / AUTO, X = R'^T when st->gate_lq (Lq holds R' of the QR
+// R^T = Q' R', so that R = R'^T Q'^T and L = R'^T) and X = R otherwise.
+__global__ void k_form_x(int n, const double* __restrict__ L, int ldl, const double* __restrict__ Lq,
+                         double* X, int precond, const DevState* st)
 {
+    const bool use_l = (precond >= MPJSVD_PRECOND_L) && *(volatile const int*)&st->gate_lq;
     size_t total = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         int i = (int)(e % n), j = (int)(e / n);
         double v;
-        if (precond == MPJSVD_PRECOND_R) v = (i <= j) ? L[cm(i, j, ldl)] : 0.0;
+        if (use_l) v = (i >= j) ? Lq[cm(j, i, n)] : 0.0;
+        else if (precond != MPJSVD_PRECOND_RT) v = (i <= j) ? L[cm(i, j, ldl)] : 0.0;
         else v = (i >= j) ? L[cm(j, i, ldl)] : 0.0;
         X[cm(i, j, n)] = v;
+    }
+}
+
+// Alg. 2's choice between X = R and X = L: gate_lq = 1 when force, or when some column of R
+// is not diagonally dominant (|r_jj| < sum_{i<j} |r_ij|: R is not "almost diagonal").
+// One warp per column.
+__global__ void k_lq_decide(int n, const double* __restrict__ L, int ldl, int force, DevState* st)
+{
+    if (call_failed(st)) return;
+    if (force) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->gate_lq = 1;
+        return;
+    }
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = warp; j < n; j += nw) {
+        double off = 0.0;
+        for (int i = lane; i < j; i += 32) off += fabs(L[cm(i, j, ldl)]);
+        off = warp_sum(off);
+        if (lane == 0 && off > fabs(L[cm(j, j, ldl)])) atomicOr(&st->gate_lq, 1);
+    }
+}
+
+// Lq = R^T (n x n, zero above the diagonal) when gate_lq: the matrix whose QR gives L.
+__global__ void k_rt_copy(int n, const double* __restrict__ L, int ldl, double* Lq, const DevState* st)
+{
+    if (call_failed(st) || !*(volatile const int*)&st->gate_lq) return;
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        Lq[cm(i, j, n)] = (i >= j) ? L[cm(j, i, ldl)] : 0.0;
     }
 }
 
@@ -113,7 +150,7 @@ __global__ void k_colnorms(int rows, int cols, const double* __restrict__ X, int
 
 // Section 3.5 tests that need no GEMM: cond_R and the trailing-norm test. Decides the branch
 // unless the orth test is still needed (branch = -1 then). One CTA.
-__global__ void k_branch_first(int n, const double* __restrict__ L, int ldl, const double* cn,
+__global__ void k_branch_first(int n, const double* __restrict__ X, const double* cn,
                                int mode, double tol_cond_coef, double trailing_frac, DevState* st)
 {
     __shared__ double red[32];
@@ -127,7 +164,8 @@ __global__ void k_branch_first(int n, const double* __restrict__ L, int ldl, con
         double m2 = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
         st->maxnorm = m2;
-        double r00 = fabs(L[cm(0, 0, ldl)]), rnn = fabs(L[cm(n - 1, n - 1, ldl)]);
+        // cond_R from the diagonal of the Jacobi input X (that of R for X = R or R^T)
+        double r00 = fabs(X[cm(0, 0, n)]), rnn = fabs(X[cm(n - 1, n - 1, n)]);
         double cond = (rnn > 0.0) ? r00 / rnn : INFINITY;
         st->cond_r = cond;
         int ntrail = (int)ceil(trailing_frac * (double)n);
@@ -306,6 +344,46 @@ __global__ void k_apply_q(bool trans, int mrows, int ncols, int k, const double*
     apply_q_cols(trans, mrows, k, Vr, ldv, tau, C, ldc, c0, c1, ident ? c0 : -1);
 }
 
+// Y1/Y2 partition of the safeguard: y_j0 = the first column j with |y_i^T y_j| > y_tol |y_i| |y_j|
+// for some i < j (G = Y^T Y, cn = column norms); n if there is none.
+__global__ void k_y_partition_init(int n, DevState* st)
+{
+    st->y_j0 = n;
+    st->y2_cols_n = n;
+}
+
+__global__ void k_y_partition(int n, const double* __restrict__ G, const double* __restrict__ cn,
+                              double y_tol, DevState* st)
+{
+    if (call_failed(st)) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = warp; j < n; j += nw) {
+        int hit = 0;
+        for (int i = lane; i < j; i += 32)
+            if (fabs(G[cm(i, j, n)]) > y_tol * cn[i] * cn[j]) hit = 1;
+        if (__any_sync(0xffffffffu, hit) && lane == 0) atomicMin(&st->y_j0, j);
+    }
+}
+
+__global__ void k_y_partition_done(int n, DevState* st)
+{
+    st->gate_y2 = (st->y_j0 < n) ? 1 : 0;
+}
+
+// Ux(:, r) = Y(:, order[r]) / sig[order[r]] (binary64; the U_X of the refinement, sorted).
+__global__ void k_make_ux(int n, const double* __restrict__ Y, const double* sig, const int* order,
+                          double* Ux, const DevState* st)
+{
+    if (call_failed(st)) return;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const int j = order[r];
+        const double sj = sig[j];
+        const double inv = (sj > 0.0) ? 1.0 / sj : 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) Ux[cm(i, r, n)] = Y[cm(i, j, n)] * inv;
+    }
+}
+
 // ---- persistent cooperative kernels
 
 __global__ void k_hhqr_piv(int m, int n, double* W, int ldw, double* tau, int* perm, DevState* st)
@@ -437,11 +515,11 @@ struct SingleLayout {
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
     L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
-    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_WY, L_COUNT
+    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_WY, L_LQ, L_TAUQ, L_COUNT
 };
 static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
 
-static SingleLayout single_layout(int m, int n, bool qr_first)
+static SingleLayout single_layout(int m, int n, bool qr_first, bool lq)
 {
     size_t nn = (size_t)n * n;
     int mq = qr_first ? n : m;
@@ -476,6 +554,8 @@ static SingleLayout single_layout(int m, int n, bool qr_first)
     sz[L_FLAGS] = sizeof(int) * n;
     sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
     sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n, m);
+    sz[L_LQ] = lq ? sizeof(double) * nn : 0;   // the QR of R^T (second preconditioning)
+    sz[L_TAUQ] = lq ? sizeof(double) * n : 0;
     // The QRCP's broadcast slots are live only during the QR preconditioning; the buffers
     // from X up to V_acc are first written after it, so the slots share their memory when
     // they fit (L_BITS, zeroed at the start of a call, is not in that span).
@@ -615,7 +695,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
 {
     const mpjsvd_params& P = h->params;
     const bool qr_first = P.qr_first && m > n;
-    SingleLayout L = single_layout(m, n, qr_first);
+    const bool lq = P.precond >= MPJSVD_PRECOND_L;
+    SingleLayout L = single_layout(m, n, qr_first, lq);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;
     char* base = (char*)h->ws;
@@ -647,6 +728,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     int* qflags = (int*)ptr(L_FLAGS);
     unsigned* ver = (unsigned*)ptr(L_VER);
     double* wy = (double*)ptr(L_WY);
+    double* Lq = (double*)ptr(L_LQ);
+    double* tauq = (double*)ptr(L_TAUQ);
     // n x n factorizations are always blocked (every n <= 12288 has a panel width); the QRCP's
     // broadcast slots may alias the stage buffers, so no unblocked kernel runs after it
     if (bqr_nb(n) == 0) return cuda_fail("blocked QR: no panel width for n", cudaErrorInvalidValue);
@@ -693,12 +776,25 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         if ((rc = launch_hhqr(h, true, mq, n, Wq, mq, tau, perm, st, -1, bcast, qflags))) return rc;
         k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
     }
-    k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, X, P.precond); ++h->launch_count;
+    if (lq) {
+        // second preconditioning (Alg. 2): R = L Q2^T from the QR of R^T, when forced or when
+        // R is not almost diagonal (decided on the device)
+        k_lq_decide<<<std::max(1, std::min(egrid, (n * 32 + T256 - 1) / T256)), T256, 0, s>>>(
+            n, WqL, mq, P.precond == MPJSVD_PRECOND_L ? 1 : 0, st); ++h->launch_count;
+        k_rt_copy<<<egrid, T256, 0, s>>>(n, WqL, mq, Lq, st); ++h->launch_count;
+        if ((rc = bqr_factor(h, n, n, Lq, n, tauq, wy, st, kGateLq + 1))) return rc;
+    }
+    k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, Lq, X, P.precond, st); ++h->launch_count;
+    h->last_precond = P.precond;
     record(h, 1);
+
+    // triangular structure of X for the GEMMs (unknown on the host for AUTO: full products)
+    const bool x_lower = P.precond == MPJSVD_PRECOND_RT || P.precond == MPJSVD_PRECOND_L;
+    const bool x_upper = P.precond == MPJSVD_PRECOND_R;
 
     // ---- [3.5] special cases
     k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, X, n, cn); ++h->launch_count;
-    k_branch_first<<<1, 1024, 0, s>>>(n, WqL, mq, cn, P.mode, P.tol_cond_coef, P.trailing_frac, st); ++h->launch_count;
+    k_branch_first<<<1, 1024, 0, s>>>(n, X, cn, P.mode, P.tol_cond_coef, P.trailing_frac, st); ++h->launch_count;
     if (P.mode == MPJSVD_MODE_AUTO) {
         k_scaled_low<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, X, Xl, st); ++h->launch_count;
         GemmArgs g;
@@ -706,8 +802,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g.A = Xl; g.lda = n; g.transA = true;
         g.B = Xl; g.ldb = n; g.C = G; g.ldc = n;
         // Xt^T Xt: X = R^T (lower) -> Xt(i, a) = 0 for i < a; X = R (upper) -> 0 for i > a
-        g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);
-        g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
+        g.klo_from_row = x_lower;
+        g.khi_from_row = x_upper;
         int tiles = ((n + kGemmBM - 1) / kGemmBM) * ((n + kGemmBN - 1) / kGemmBN);
         // gate on branch == -1 is checked inside k_orth_max/k_branch_final; the Gram runs
         // unconditionally in auto mode (one FP32 GEMM, cheap)
@@ -724,8 +820,10 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // the register file bounds the width for tall X: fall back to narrower blocks
     // binary32 stage: the blocked tensor-core form (64-column blocks) or register-resident
     // level-1 visits
-    const bool low_tc = P.low_kernel == MPJSVD_LOWK_TC ||
-                        (P.low_kernel == MPJSVD_LOWK_AUTO && n >= kLowTcMinN);
+    // (the alternative switch needs the stage's V: register-resident visits replay it)
+    const bool alt_switch = P.switch_method == MPJSVD_SWITCH_V;
+    const bool low_tc = !alt_switch && (P.low_kernel == MPJSVD_LOWK_TC ||
+                                        (P.low_kernel == MPJSVD_LOWK_AUTO && n >= kLowTcMinN));
     int w_low = low_tc ? 64 : sweep_fit_w_f32(n, pick_w(n, n, true, h->num_sms, P.block_w));
     int w_work = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
     if (w_low == 0 || w_work == 0)
@@ -740,33 +838,53 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         Dl.k = sweep_blocks(n, w_low); Dl.maxsweep = std::min(P.maxsweep, 64); Dl.tol = tol_low;
         Dl.stop = P.stop;
         Dl.dsc = dsc; Dl.alph = alph; Dl.ver = ver;
-        if (low_tc) {
-            if ((rc = launch_bsweeps_tf32(h, Dl, Xl, st, 0, 1))) return rc;
+        if (alt_switch) {
+            // the stage also accumulates its rotations into V_low (binary64 copy of the binary32
+            // rotations), kept in B's buffer
+            Dl.nV = n;
+            k_identity<<<egrid, T256, 0, s>>>(n, Bq, st, 1); ++h->launch_count;
+            if ((rc = launch_sweeps_f32v(h, Dl, Xl, Bq, st, 0, 1))) return rc;
+            record(h, 3);
+            // ---- [3.3] the alternative switch: V_low = Q R2, V_acc = Q, Y = X Q
+            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
+            k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
+            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
+            GemmArgs g2;
+            g2.M = n; g2.N = n; g2.K = n;
+            g2.A = X; g2.lda = n; g2.transA = false;
+            g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
+            g2.klo_from_row = x_upper;
+            g2.khi_from_row = x_lower;
+            if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
         } else {
-            if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
+            if (low_tc) {
+                if ((rc = launch_bsweeps_tf32(h, Dl, Xl, st, 0, 1))) return rc;
+            } else {
+                if ((rc = launch_sweeps_f32(h, Dl, Xl, st, 0, 1, nullptr))) return rc;
+            }
+            k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
+            k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
+            k_make_ul<<<std::min(n, egrid), T256, 0, s>>>(n, Xl, sigl, ord, Ul, st); ++h->launch_count;
+            record(h, 3);
+            // ---- [3.3] switch: B = X^T U_low; B = Q R2; V_acc = Q; Y = X Q
+            GemmArgs g;
+            g.M = n; g.N = n; g.K = n;
+            g.A = X; g.lda = n; g.transA = true;
+            g.B = Ul; g.ldb = n; g.C = Bq; g.ldc = n;
+            g.klo_from_row = x_lower;  // X^T upper when X lower
+            g.khi_from_row = x_upper;
+            if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
+            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
+            k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
+            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
+            GemmArgs g2;
+            g2.M = n; g2.N = n; g2.K = n;
+            g2.A = X; g2.lda = n; g2.transA = false;
+            g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
+            g2.klo_from_row = x_upper;  // X upper: X(i, k) = 0 for k < i
+            g2.khi_from_row = x_lower;  // X lower: X(i, k) = 0 for k > i
+            if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
         }
-        k_colnorms_gated<float><<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Xl, n, sigl, st); ++h->launch_count;
-        k_rank_desc<float><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sigl, ord, st, 1); ++h->launch_count;
-        k_make_ul<<<std::min(n, egrid), T256, 0, s>>>(n, Xl, sigl, ord, Ul, st); ++h->launch_count;
-        record(h, 3);
-        // ---- [3.3] switch: B = X^T U_low; B = Q R2; V_acc = Q; Y = X Q
-        GemmArgs g;
-        g.M = n; g.N = n; g.K = n;
-        g.A = X; g.lda = n; g.transA = true;
-        g.B = Ul; g.ldb = n; g.C = Bq; g.ldc = n;
-        g.klo_from_row = (P.precond != MPJSVD_PRECOND_R);  // X^T upper when X lower
-        g.khi_from_row = (P.precond == MPJSVD_PRECOND_R);
-        if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
-        if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
-        k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
-        if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
-        GemmArgs g2;
-        g2.M = n; g2.N = n; g2.K = n;
-        g2.A = X; g2.lda = n; g2.transA = false;
-        g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
-        g2.klo_from_row = (P.precond == MPJSVD_PRECOND_R);  // X upper: X(i, k) = 0 for k < i
-        g2.khi_from_row = (P.precond != MPJSVD_PRECOND_R);  // X lower: X(i, k) = 0 for k > i
-        if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
     } else {
         record(h, 3);
     }
@@ -784,13 +902,72 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     Dw.k = sweep_blocks(n, w_work); Dw.maxsweep = std::min(P.maxsweep, 64); Dw.tol = tol_work;
     Dw.stop = P.stop;
     Dw.dsc = dsc; Dw.alph = alph; Dw.ver = ver;
-    if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
+    if (P.y_tol > 0.0) {
+        // Y1/Y2 safeguard (Section 3.4): Y2 = the columns of Y from the first one whose largest
+        // cosine with an earlier column exceeds y_tol; Alg. 1 on Y2 (with its columns of V),
+        // then one pass over the pairs between Y1 and Y2, then the refinement as usual. The
+        // Gram Y^T Y goes to B's buffer (dead after the switch); j0 stays on the device.
+        k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Y, n, cn); ++h->launch_count;
+        GemmArgs gy;
+        gy.M = n; gy.N = n; gy.K = n;
+        gy.A = Y; gy.lda = n; gy.transA = true;
+        gy.B = Y; gy.ldb = n; gy.C = Bq; gy.ldc = n;
+        gy.klo_from_row = gy.khi_from_row = false;
+        if ((rc = launch_gemm_d(h, gy, nullptr, 0))) return rc;
+        k_y_partition_init<<<1, 1, 0, s>>>(n, st); ++h->launch_count;  // also records n
+        k_y_partition<<<std::max(1, std::min(egrid, (n * 32 + T256 - 1) / T256)), T256, 0, s>>>(
+            n, Bq, cn, P.y_tol, st); ++h->launch_count;
+        k_y_partition_done<<<1, 1, 0, s>>>(n, st); ++h->launch_count;
+        SweepDims Dy = Dw;
+        Dy.filter = 1;
+        Dy.j0 = &st->y_j0;
+        if ((rc = launch_sweeps_f64(h, Dy, Y, Vacc, st, 2, kGateY2 + 1, nullptr))) return rc;
+        Dy.filter = 2;
+        Dy.maxsweep = 1;
+        if ((rc = launch_sweeps_f64(h, Dy, Y, Vacc, st, 2, kGateY2 + 1, nullptr))) return rc;
+    }
+    if (!P.v_by_qr) {
+        if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
+    } else {
+        // V from the QR of X^T U_X (Section 3.4): Alg. 1 on Y without V; U_X = the normalized
+        // columns of Y sorted by descending norm; B3 = X^T U_X = Q3 R3; Y = X Q3 and Alg. 1
+        // with V accumulated from V_acc = Q3
+        SweepDims Dn = Dw;
+        Dn.nV = 0;
+        if ((rc = launch_sweeps_f64(h, Dn, Y, nullptr, st, 1, -1, nullptr))) return rc;
+        k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Y, n, sig); ++h->launch_count;
+        k_rank_desc<double><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sig, ord2, st, -1); ++h->launch_count;
+        k_make_ux<<<std::min(n, egrid), T256, 0, s>>>(n, Y, sig, ord2, Ul, st); ++h->launch_count;
+        GemmArgs g3;
+        g3.M = n; g3.N = n; g3.K = n;
+        g3.A = X; g3.lda = n; g3.transA = true;
+        g3.B = Ul; g3.ldb = n; g3.C = Bq; g3.ldc = n;
+        g3.klo_from_row = x_lower;
+        g3.khi_from_row = x_upper;
+        if ((rc = launch_gemm_d(h, g3, nullptr, 0))) return rc;
+        if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, -1))) return rc;
+        k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, -1); ++h->launch_count;
+        if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, -1))) return rc;
+        GemmArgs g4;
+        g4.M = n; g4.N = n; g4.K = n;
+        g4.A = X; g4.lda = n; g4.transA = false;
+        g4.B = Vacc; g4.ldb = n; g4.C = Y; g4.ldc = n;
+        g4.klo_from_row = x_upper;
+        g4.khi_from_row = x_lower;
+        if ((rc = launch_gemm_d(h, g4, nullptr, 0))) return rc;
+        if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 2, -1, nullptr))) return rc;
+    }
     record(h, 5);
 
     // ---- Sigma, U_X, sort, U = Q [U_R; 0], V = P V_R
     k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Y, n, sig); ++h->launch_count;
     k_rank_desc<double><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sig, ord2, st, -1); ++h->launch_count;
-    k_finalize<<<std::min(n, egrid), T256, 0, s>>>(m, n, Y, Vacc, sig, ord2, perm, P.precond, U, S, V, st); ++h->launch_count;
+    if (lq) {
+        // X = L = R Q': R = U_X Sigma (Q' V_acc)^T, so V_R = Q' V_acc
+        if ((rc = bqr_apply(h, n, n, n, Lq, n, tauq, Vacc, n, false, wy, st, kGateLq + 1))) return rc;
+    }
+    k_finalize<<<std::min(n, egrid), T256, 0, s>>>(m, n, Y, Vacc, sig, ord2, perm,
+                                                    lq ? MPJSVD_PRECOND_R : P.precond, U, S, V, st); ++h->launch_count;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("finalize kernels", e);
     if (qr_first) {
@@ -852,6 +1029,8 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
     return e == cudaSuccess ? 0 : cuda_fail("geqp3 kernels", e);
 }
 
+static int n_minus_j0(const DevState& st) { return st.gate_y2 ? st.y2_cols_n - st.y_j0 : 0; }
+
 int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
 {
     DevState st;
@@ -873,6 +1052,11 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     r.block_w_work = h->last_block_w_work;
     r.launches = h->launch_count;
     r.qrcp = h->last_qrcp;
+    r.precond = h->last_precond >= MPJSVD_PRECOND_L ? (st.gate_lq ? MPJSVD_PRECOND_L : MPJSVD_PRECOND_R)
+                                                    : h->last_precond;
+    r.sweeps_v = st.sweeps_v;
+    r.rot_v = (long long)st.rot_v;
+    r.y2_cols = h->params.y_tol > 0.0 ? n_minus_j0(st) : 0;
     r.n_flagged = -1;
     if (h->last_flag_dev) {
         e = cudaMemcpy(&r.n_flagged, h->last_flag_dev, sizeof(int), cudaMemcpyDeviceToHost);
@@ -945,7 +1129,8 @@ static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double
     mpjsvd_default_params(&ctx.params);
     // the workspace svd_single will ask for, from the same parameters it reads
     const size_t state_bytes = align256(sizeof(DevState));
-    const size_t need = single_layout(m, n, ctx.params.qr_first && m > n).total;
+    const size_t need = single_layout(m, n, ctx.params.qr_first && m > n,
+                                      ctx.params.precond >= MPJSVD_PRECOND_L).total;
     if (state_bytes + need > kNoAllocBytes)
         return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
                          cudaErrorInvalidValue);

@@ -250,6 +250,11 @@ struct SweepDims {
     void* dsc;   // T[n]: column scales, 1 at the start of the stage
     void* alph;  // T[n]: tracked squared norms (true scale)
     unsigned* ver;  // 2k block versions, X then V (cooperative single-matrix launch only)
+    // pair filter (the Y1/Y2 safeguard of Section 3.4): 0 every pair; 1 only pairs of columns
+    // >= *j0 (Alg. 1 on Y2); 2 only pairs with one column < *j0 and one >= *j0 (one pass over
+    // the pairs between Y1 and Y2). j0: device int, read when a visit starts.
+    int filter = 0;
+    const int* j0 = nullptr;
 };
 
 constexpr int kMaxWarps = 32;
@@ -268,6 +273,8 @@ struct VisitShared {
     unsigned act[2 * W];        // active-pair mask per inner round
     int flags[4];               // [0] rotations, [1] norms need recomputing
     unsigned mxc, mxt;          // binary32 bits: largest cosine and |tan| rotated in the visit
+    unsigned char side[2 * W];  // pair filter 2: 1 for a column < j0
+    int cross_only;             // pair filter 2 active
 };
 
 // Pair p of an inner round. Cross rounds: (p, W + (p + q) % W). Intra rounds (W even,
@@ -340,7 +347,7 @@ __device__ __forceinline__ void inner_round(T (&x)[RPT][2 * W], bool intra, int 
         const int a = pair_a<W>(intra, q, p), b = pair_b<W>(intra, q, p);
         unsigned act = 0;
         float cs = 0.0f, ta = 0.0f;  // cosine and |tan| of this pair's rotation (stopping rule)
-        if (sm.gidx[a] >= 0 && sm.gidx[b] >= 0) {
+        if (sm.gidx[a] >= 0 && sm.gidx[b] >= 0 && (!sm.cross_only || sm.side[a] != sm.side[b])) {
             const T gh = short_sum(sm.part[p], nw);
             const T da = sm.d[a], db = sm.d[b];
             const T ia = sm.dinv[a], ib = sm.dinv[b];
@@ -462,6 +469,11 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
         int blk = (tid < W) ? bi : bj;
         int c = blk * W + (tid < W ? tid : tid - W);
         bool ok = (blk * W < D.n) && (c < D.n);
+        if (D.filter != 0) {
+            const int j0 = *(volatile const int*)D.j0;
+            if (D.filter == 1 && c < j0) ok = false;  // Y1 columns stay as they are
+            sm.side[tid] = (unsigned char)(c < j0);
+        }
         sm.gidx[tid] = ok ? c : -1;
         T dc = ok ? __ldcg(dsc + c) : T(1);
         sm.d[tid] = dc;
@@ -474,6 +486,7 @@ __device__ int jacobi_visit_x(const SweepDims& D, T* X, int bi, int bj, bool fir
         sm.flags[1] = 0;
         sm.mxc = 0u;
         sm.mxt = 0u;
+        sm.cross_only = (D.filter == 2);
     }
     __syncthreads();
 

@@ -67,4 +67,28 @@ int launch_sweeps_f32(mpjsvd_ctx* h, const SweepDims& D, float* X, DevState* st,
     return cuda_fail("sweep: no binary32 variant fits (block width, rows)", cudaErrorInvalidValue);
 }
 
+// The binary32 stage that also accumulates its rotations into V (binary64, n rows; the
+// alternative switch of Section 3.3 takes the QR of that V). Block widths 4 and 8.
+int launch_sweeps_f32v(mpjsvd_ctx* h, const SweepDims& D, float* X, double* V, DevState* st, int phase,
+                       int gate_want)
+{
+    const int w = D.w >= 8 ? 8 : 4;
+    SweepDims Dv = D;
+    Dv.w = w;
+    Dv.k = std::max(2, (D.n + w - 1) / w + (((D.n + w - 1) / w) & 1));
+    for (int rpt = 2; rpt <= 8; rpt *= 2) {
+        if ((D.mX + rpt - 1) / rpt > 1024) continue;
+        const int threads = sweep_threads(D.mX, rpt);
+        int rc = -1;
+#define MPJ_V(WW, RR) \
+        if (w == WW && rpt == RR) rc = launch_sweeps_wr<float, true, WW, RR>(h, Dv, X, V, st, phase, gate_want, threads)
+        MPJ_V(4, 2); MPJ_V(4, 4); MPJ_V(4, 8);
+        MPJ_V(8, 2); MPJ_V(8, 4); MPJ_V(8, 8);
+#undef MPJ_V
+        if (rc == kSweepTooManyThreads) continue;
+        return rc;
+    }
+    return cuda_fail("sweep: no binary32 variant with V fits", cudaErrorInvalidValue);
+}
+
 }  // namespace mpj

@@ -23,12 +23,19 @@ __global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, 
 {
     __shared__ VisitShared<T, W> sm;
     if (call_failed(st)) return;
-    if (gate_want >= 0 && *(volatile int*)&st->gate_low != gate_want) return;
+    if (!gate_open(st, gate_want)) return;
     Group g{(int)blockIdx.x, (int)gridDim.x, st};
-    // persistent scales start at 1, block versions at 0
+    // persistent scales start at 1, block versions at 0, the phase's per-sweep records at 0 (a
+    // phase may run more than once in a call)
     T* dsc = (T*)D.dsc;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += gridDim.x * blockDim.x) dsc[j] = T(1);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 2 * D.k; b += gridDim.x * blockDim.x) D.ver[b] = 0u;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+            st->rot_sweep[phase][i] = 0ull;
+            st->mx_cos[phase][i] = 0u;
+            st->mx_tan[phase][i] = 0u;
+        }
     if (!g.sync()) return;
     bool conv = false;
     int sweeps = jacobi_sweeps_flow<T, WITH_V, W, RPT>(g, D, X, V, st->rot_sweep[phase], st->mx_cos[phase],
@@ -39,8 +46,10 @@ __global__ void k_sweeps(SweepDims D, T* X, double* V, DevState* st, int phase, 
         unsigned long long tot = 0;
         for (int s = 0; s < sweeps; ++s) tot += __ldcg(&st->rot_sweep[phase][s]);
         if (phase == 0) { st->sweeps_low = sweeps; st->rot_low = tot; }
-        else { st->sweeps_work = sweeps; st->rot_work = tot; }
-        if (!conv) atomicOr(&st->status, MPJSVD_STATUS_NOT_CONVERGED);
+        else if (phase == 1) { st->sweeps_work = sweeps; st->rot_work = tot; }
+        else { st->sweeps_v += sweeps; st->rot_v += tot; }
+        // a one-pass launch (the safeguard's pass over the Y1 x Y2 pairs) is complete by design
+        if (!conv && D.filter != 2) atomicOr(&st->status, MPJSVD_STATUS_NOT_CONVERGED);
     }
 }
 

@@ -18,10 +18,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libmpjsvd.so")
 
 MODE = {"auto": 0, "mixed": 1, "plain": 2}
-PRECOND = {"rt": 0, "r": 1}
+PRECOND = {"rt": 0, "r": 1, "l": 2, "auto": 3}
 QRCP = {"mixed": 0, "f64": 1}
 STOP = {"xgesvj": 0, "alg1": 1}
 LOWK = {"auto": 0, "tc": 1, "reg": 2}
+SWITCH = {"u": 0, "v": 1}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -38,7 +39,8 @@ class Params(ctypes.Structure):
                 ("maxsweep", ctypes.c_int), ("block_w", ctypes.c_int), ("mode", ctypes.c_int),
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
                 ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
-                ("low_kernel", ctypes.c_int)]
+                ("low_kernel", ctypes.c_int), ("v_by_qr", ctypes.c_int),
+                ("switch_method", ctypes.c_int), ("y_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("ms_branch", ctypes.c_float), ("ms_low", ctypes.c_float),
                 ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
                 ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int),
-                ("n_flagged", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("sweeps_v", ctypes.c_int), ("rot_v", ctypes.c_longlong),
+                ("y2_cols", ctypes.c_int), ("n_flagged", ctypes.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -119,6 +122,8 @@ def mpjsvd_default_params(**overrides):
             v = STOP[v]
         if k == "low_kernel" and isinstance(v, str):
             v = LOWK[v]
+        if k == "switch_method" and isinstance(v, str):
+            v = SWITCH[v]
         setattr(p, k, v)
     return p
 
@@ -254,6 +259,8 @@ class Handle:
                 v = STOP[v]
             if k == "low_kernel" and isinstance(v, str):
                 v = LOWK[v]
+            if k == "switch_method" and isinstance(v, str):
+                v = SWITCH[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 

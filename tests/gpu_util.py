@@ -7,10 +7,10 @@ U64 = 2.0 ** -53
 
 
 def gpu_svd(A, mode="auto", precond="rt", qr_first=0, block_w=0, tol=0.0, maxsweep=30, stats=True,
-            qrcp="mixed", stop="xgesvj", low_kernel="auto"):
+            qrcp="mixed", stop="xgesvj", low_kernel="auto", **params):
     from paper_2209_04626_gb300 import mpjsvd
     h = mpjsvd.Handle(mode=mode, precond=precond, qr_first=qr_first, block_w=block_w,
-                      maxsweep=maxsweep, qrcp=qrcp, stop=stop, low_kernel=low_kernel)
+                      maxsweep=maxsweep, qrcp=qrcp, stop=stop, low_kernel=low_kernel, **params)
     Ad = mpjsvd.colmajor(torch.from_numpy(np.asarray(A, dtype=np.float64)), torch.device("cuda"))
     U, S, V = h.svd(Ad, tol=tol)
     st = h.stats() if stats else None

@@ -19,9 +19,12 @@ from tests.gpu_util import (U64, align_signs, check_factorization, check_sign_ru
 pytestmark = pytest.mark.gpu
 
 
-def _compare(A, mode, precond="rt", qr_first=0, block_w=0, vec_tol=1e-8):
-    U, S, V, st = gpu_svd(A, mode=mode, precond=precond, qr_first=qr_first, block_w=block_w)
-    Uo, So, Vo, sto = oracle.svd(A, mode=mode, precond=precond)
+def _compare(A, mode, precond="rt", qr_first=0, block_w=0, vec_tol=1e-8, **opts):
+    U, S, V, st = gpu_svd(A, mode=mode, precond=precond, qr_first=qr_first, block_w=block_w, **opts)
+    oopts = {k: v for k, v in opts.items() if k in ("y_tol", "v_by_qr")}
+    if "switch_method" in opts:
+        oopts["switch_method"] = {"u": 0, "v": 1}[opts["switch_method"]]
+    Uo, So, Vo, sto = oracle.svd(A, mode=mode, precond=precond, **oopts)
     assert st["status"] == 0, st
     check_factorization(A, U, S, V)
     check_sign_rule(V)
@@ -59,12 +62,38 @@ def test_small_shapes(n, mode):
     _compare(A, mode)
 
 
-@pytest.mark.parametrize("precond", ["rt", "r"])
+@pytest.mark.parametrize("precond", ["rt", "r", "l", "auto"])
 @pytest.mark.parametrize("qr_first", [0, 1])
 def test_preconditioner_variants(precond, qr_first):
     rng = np.random.default_rng(7)
     A = inputs.known_sigma(rng, 150, 96, np.logspace(0, -5, 96))
-    _compare(A, "mixed", precond=precond, qr_first=qr_first)
+    st, sto = _compare(A, "mixed", precond=precond, qr_first=qr_first)
+    assert st["precond"] == sto["precond"], (st["precond"], sto["precond"])
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain", "auto"])
+def test_second_preconditioning_choice(mode):
+    """Alg. 2's choice on the device: X = R when every column of R is diagonally dominant (a
+    matrix with nearly orthogonal, graded columns), X = L from the LQ of R otherwise; the
+    choice, the branch and the SVD match the oracle's."""
+    rng = np.random.default_rng(17)
+    near_diag = inputs.orthonormal(rng, 120, 80) * np.logspace(0, -3, 80) + \
+        1e-7 * rng.standard_normal((120, 80))
+    dense = inputs.known_sigma(rng, 120, 80, np.logspace(0, -4, 80))
+    for A, want in ((near_diag, 1), (dense, 2)):
+        st, sto = _compare(np.asfortranarray(A), mode, precond="auto")
+        assert st["precond"] == sto["precond"] == want, (st["precond"], sto["precond"])
+
+
+def test_lq_at_full_size():
+    """X = L on the 2048 x 1024 workload: the blocked QR of R^T, the Jacobi stages on L and
+    V = P Q' V_acc, against the oracle run with the same second preconditioning."""
+    A = inputs.precision_2048x1024()
+    U, S, V, st = gpu_svd(A, mode="mixed", precond="l")
+    Uo, So, Vo, sto = oracle.svd(A, mode="mixed", precond="l")
+    assert st["status"] == 0 and st["precond"] == 2, st
+    check_factorization(A, U, S, V)
+    assert np.max(np.abs(S - So) / So) <= 1e-12
 
 
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
@@ -179,3 +208,51 @@ def test_binary32_stage_resolves_small_columns():
     check_factorization(A, U, S, V)
     sigma_gate(A, S, So)
     assert st["sweeps_work"] <= sto["sweeps_work"] + 1, (st["sweeps_work"], sto["sweeps_work"])
+
+
+@pytest.mark.parametrize("opts", [dict(v_by_qr=1), dict(y_tol=1e-6), dict(y_tol=1e-6, v_by_qr=1)])
+def test_refinement_variants(opts):
+    """Section 3.4's variants on the GPU against the oracle run with the same options: V from
+    the QR of X^T U_X after a refinement without V, and the Y1/Y2 safeguard (y_tol = 1e-6
+    activates it on the 256 x 128 workload: Alg. 1 on Y2, one pass over the Y1 x Y2 pairs)."""
+    A, _ = inputs.plain_256x128()
+    st, sto = _compare(A, "mixed", **opts)
+    if opts.get("v_by_qr"):
+        assert st["sweeps_v"] >= 1 and sto["sweeps_v"] >= 1
+    if opts.get("y_tol"):
+        # the partition depends on Y after the switch, which each side computes from its own
+        # binary32 stage (round-robin on the GPU, cyclic in the oracle): both must activate
+        assert st["y2_cols"] > 0 and sto["y2_cols"] > 0, (st["y2_cols"], sto["y2_cols"])
+
+
+def test_safeguard_inactive_is_a_no_op():
+    """With y_tol above every cosine of Y after the switch, the safeguard changes nothing: the
+    same singular values, bit for bit, as without it."""
+    A, _ = inputs.plain_256x128()
+    U0, S0, V0, st0 = gpu_svd(A, "mixed")
+    U1, S1, V1, st1 = gpu_svd(A, "mixed", y_tol=0.5)
+    assert st1["y2_cols"] == 0 and st1["sweeps_v"] == 0
+    assert np.array_equal(S0, S1) and np.array_equal(V0, V1)
+
+
+@pytest.mark.parametrize("method", ["u", "v"])
+def test_switch_methods(method):
+    """The two precision switches of Section 3.3 against the oracle run with the same switch:
+    the same SVD; the refinement after the switch the paper prefers (QR of X^T U_low) needs no
+    more rotations than after the alternative (QR of the binary32 stage's V)."""
+    A, _ = inputs.plain_256x128()
+    st, sto = _compare(A, "mixed", switch_method=method)
+    assert st["branch"] == 0 and st["sweeps_low"] > 0
+
+
+def test_switch_comparison():
+    A = inputs.precision_2048x1024(m=1024, n=512)
+    res = {}
+    for method in ("u", "v"):
+        U, S, V, st = gpu_svd(A, "mixed", switch_method=method)
+        assert st["status"] == 0
+        check_factorization(A, U, S, V)
+        res[method] = (S, st)
+    (Su, stu), (Sv, stv) = res["u"], res["v"]
+    assert np.max(np.abs(Su - Sv) / Su) <= 1e-12
+    assert stu["rot_work"] <= stv["rot_work"], (stu["rot_work"], stv["rot_work"])
