@@ -187,7 +187,10 @@ int mpjsvd_svd(mpjsvd_handle h, int m, int n, const double* A, int lda, double* 
                double* V, double tol);
 
 /* Thin SVDs of `batch` independent matrices of uneven sizes in one persistent launch
- * (one CTA per matrix, largest first).
+ * (one CTA per matrix, largest first). With params.block_w = 0 the first call that contains
+ * a size class of n tunes it (host-synchronizing: each kernel variant runs on a sample of the
+ * class; see mpjsvd_get_batched_tuning); params.qrcp selects Alg. 5 (default) or binary64
+ * Businger-Golub for the RRQR; params.precond must be RT or R.
  *   m, n, lda : HOST arrays of length batch (1 <= n_i <= m_i <= 1024, n_i <= 512,
  *               lda_i >= m_i)
  *   A, U, S, V: DEVICE arrays of length batch holding device pointers laid out as in
@@ -198,6 +201,27 @@ int mpjsvd_svd(mpjsvd_handle h, int m, int n, const double* A, int lda, double* 
 int mpjsvd_svd_batched(mpjsvd_handle h, int batch, const int* m, const int* n, const int* lda,
                        const double* const* A, double* const* U, double* const* S,
                        double* const* V, double tol, int* info);
+
+/* mpjsvd_svd_batched with the sizes in DEVICE memory (the layout of the hot-path table's
+ * boundary): nothing is read or copied on the host, so once a call of the same batch, max_m and
+ * max_n has run (its workspace then exists) the call can be captured in a CUDA graph and
+ * replayed. The order of the work queue (largest n^2 m first) is computed on the device.
+ *   max_m, max_n : HOST bounds of the sizes, 1 <= max_n <= max_m <= 1024, max_n <= 512
+ *   m, n, lda : DEVICE int arrays of length batch; a matrix whose sizes fall outside the
+ *               bounds (or n < 1, m < n, lda < m) is not computed and gets info = -1
+ *   A, U, S, V, tol, info : as in mpjsvd_svd_batched
+ * Uses the kernel variants the handle's autotuner picked in an earlier mpjsvd_svd_batched call
+ * (the defaults otherwise). */
+int mpjsvd_svd_batched_dev(mpjsvd_handle h, int batch, int max_m, int max_n, const int* m, const int* n,
+                           const int* lda, const double* const* A, double* const* U, double* const* S,
+                           double* const* V, double tol, int* info);
+
+/* The batched autotuner's picks (params.block_w = 0): per size class of n (<= 32, <= 64,
+ * <= 128, <= 256, <= 512), the block widths of the binary32 and binary64 stages that ran
+ * fastest on a sample of the class's matrices in the first mpjsvd_svd_batched call that
+ * contained the class, and that sample's time (ms). 0 for a class not tuned yet. Any pointer
+ * may be NULL; each array has 5 entries. */
+int mpjsvd_get_batched_tuning(mpjsvd_handle h, int* w_low, int* w_work, float* ms);
 
 /* Adjoint of the thin SVD (not part of the paper). Given U (m x n), S (n, descending,
  * positive), V (n x n) from mpjsvd_svd and the cotangents gU (m x n), gS (n), gV (n x n)

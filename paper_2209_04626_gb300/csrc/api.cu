@@ -233,6 +233,39 @@ int mpjsvd_svd_batched(mpjsvd_handle h, int batch, const int* m, const int* n, c
     return svd_batched(h, batch, m, n, lda, A, U, S, V, tol, info);
 }
 
+int mpjsvd_svd_batched_dev(mpjsvd_handle h, int batch, int max_m, int max_n, const int* m, const int* n,
+                           const int* lda, const double* const* A, double* const* U, double* const* S,
+                           double* const* V, double tol, int* info)
+{
+    if (!h) return -1;
+    if (batch < 0) return -2;
+    if (batch == 0) return 0;
+    if (max_m < 1 || max_m > 1024) return -3;
+    if (max_n < 1 || max_n > 512 || max_n > max_m) return -4;
+    if (!m) return -5;
+    if (!n) return -6;
+    if (!lda) return -7;
+    if (!A) return -8;
+    if (!U) return -9;
+    if (!S) return -10;
+    if (!V) return -11;
+    if (!(tol <= 0.0 || (tol > 0.0 && tol < 1.0))) return -12;
+    if (!info) return -13;
+    if (h->params.precond > MPJSVD_PRECOND_R) {
+        set_last_error("mpjsvd_svd_batched_dev: params.precond L and AUTO are single-matrix only",
+                       cudaErrorInvalidValue);
+        return -1;
+    }
+    return svd_batched_dev(h, batch, max_m, max_n, m, n, lda, A, U, S, V, tol, info);
+}
+
+int mpjsvd_get_batched_tuning(mpjsvd_handle h, int* w_low, int* w_work, float* ms)
+{
+    if (!h) return -1;
+    batched_tuning(h, w_low, w_work, ms);
+    return 0;
+}
+
 int mpjsvd_svd_backward(mpjsvd_handle h, int m, int n, const double* U, const double* S,
                         const double* V, const double* gU, const double* gS, const double* gV,
                         double* gA, double gap_tol, int* n_flagged)

@@ -33,6 +33,11 @@ struct mpjsvd_ctx {
     int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
     int last_precond;  // MPJSVD_PRECOND_* of the last call (AUTO resolved from the device)
     int* last_flag_dev;  // device count of near-degenerate flags of the last svd_backward
+    // batched autotuner: per size class of n (<= 32, 64, 128, 256, 512), the kernel variant
+    // (block widths of the two Jacobi stages) picked by timing, and its sample time
+    bool bt_tuned[5];
+    int bt_variant[5];
+    float bt_ms[5];
     // the blocked QR's look-ahead: the critical chain (panels and the updates of the next
     // panel) on a high-priority stream, the wide trailing updates on a low-priority one;
     // both fork from and join back into `stream` through events
@@ -101,6 +106,11 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
 int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,
                 const double* const* A, double* const* U, double* const* S, double* const* V,
                 double tol, int* info);
+
+int svd_batched_dev(mpjsvd_ctx* h, int batch, int max_m, int max_n, const int* m, const int* n, const int* lda,
+                    const double* const* A, double* const* U, double* const* S, double* const* V, double tol,
+                    int* info);
+void batched_tuning(const mpjsvd_ctx* h, int* w_low, int* w_work, float* ms);
 
 // adjoint (adjoint.cu)
 int svd_backward(mpjsvd_ctx* h, int m, int n, const double* U, const double* S, const double* V,

@@ -25,8 +25,19 @@
 namespace mpj {
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchWLow = 8;
-constexpr int kBatchWWork = 8;
+// Kernel variants (block widths of the two Jacobi stages), chosen per size class of n by the
+// autotuner: variant v runs binary32 blocks of kVarWLow[v] and binary64 blocks of kVarWWork[v].
+constexpr int kBatchVariants = 4;
+__host__ __device__ constexpr int var_wlow(int v) { return (v & 1) ? 16 : 8; }
+__host__ __device__ constexpr int var_wwork(int v) { return (v & 2) ? 8 : 4; }
+constexpr int kBatchDefaultVariant = 2;  // (8, 8)
+// size classes of n: <= 32, <= 64, <= 128, <= 256, <= 512
+__host__ __device__ inline int size_class(int n)
+{
+    return n <= 32 ? 0 : (n <= 64 ? 1 : (n <= 128 ? 2 : (n <= 256 ? 3 : 4)));
+}
+
+constexpr int kBatchClasses = 5;
 
 struct BatchArgs {
     int batch;
@@ -45,12 +56,13 @@ struct BatchArgs {
     int max_m, max_n;
     mpjsvd_params P;
     double tol;
+    int variant[kBatchClasses];  // per size class of n
 };
 
 // Offsets inside a slot for (max_m, max_n).
 struct SlotLayout {
     size_t st, wq, wql, tau, perm, x, xl, g, cn, sigl, ord, ul, bq, tau2, perm2, y, vacc, sig,
-        ord2, dsc, alph, total;
+        ord2, dsc, alph, wl, vn, total;
 };
 
 __host__ __device__ inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -86,6 +98,8 @@ __host__ __device__ inline SlotLayout slot_layout(int M, int N)
     L.ord2 = put(4 * (size_t)N);
     L.dsc = put(8 * (size_t)N);
     L.alph = put(8 * (size_t)N);
+    L.wl = put(4 * mn);            // lower(A) of Alg. 5's pivot search
+    L.vn = put(8 * (size_t)N);     // its two norm arrays
     L.total = o;
     return L;
 }
@@ -197,6 +211,195 @@ __device__ void cta_finalize(int m, int n, const double* Y, const double* Vacc, 
     }
 }
 
+// |x(lo:len)| of a binary32 column by one warp, on entries scaled by the power of two of their
+// maximum (no square underflows or overflows: single-precision LAPACK's convention).
+__device__ __forceinline__ float warp_norm_scaled(const float* x, int lo, int len)
+{
+    const int lane = threadIdx.x & 31;
+    float a = 0.0f;
+    for (int i = lo + lane; i < len; i += 32) a = fmaxf(a, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if (a == 0.0f) return 0.0f;
+    const float sc = __int_as_float((254 - ((__float_as_int(a) >> 23) & 0xff)) << 23);  // a sc in [1, 2)
+    float s = 0.0f;
+    for (int i = lo + lane; i < len; i += 32) {
+        const float y = x[i] * sc;
+        s = fmaf(y, y, s);
+    }
+    s = warp_sum(s);
+    return sqrtf(s) / sc;
+}
+
+// Alg. 5, step 2, for one matrix by one CTA: the Businger-Golub pivot order of lower(A) in
+// binary32 (A scaled by the power of two that brings max |a_ij| into [1, 2)), columns in the
+// CTA's workspace (global memory, L2-resident). The rules of the binary64 kernels: the first
+// maximum of the norms (in current column order) is the pivot; norms are downdated by the new
+// row entry and recomputed when the downdate keeps less than half of the binary32 digits; the
+// reflector's convention is that of the binary64 QR. Only perm (the pivot order) is kept.
+__device__ void cta_qrcp_pivots_f32(int m, int n, const double* A, int lda, float* Lw, float* vn1,
+                                    float* vn2, int* perm)
+{
+    __shared__ double s_dmax[32];
+    __shared__ float s_bv[32];
+    __shared__ int s_bi[32];
+    __shared__ int s_p;
+    __shared__ float s_tj, s_den;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    const float tol3z = 2.44140625e-04f;  // sqrt(2^-24)
+    double am = 0.0;
+    for (size_t e = tid; e < (size_t)m * n; e += nthr) am = fmax(am, fabs(A[cm((int)(e % m), (int)(e / m), lda)]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if (lane == 0) s_dmax[wid] = am;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int w = 0; w < nw; ++w) a = fmax(a, s_dmax[w]);
+        s_dmax[0] = a;
+    }
+    __syncthreads();
+    const double amax = s_dmax[0];
+    const int eb = (__double2hiint(amax) >> 20) & 0x7ff;
+    const double scale = (amax > 0.0) ? __hiloint2double((2046 - min(max(eb, 1), 2045)) << 20, 0) : 1.0;
+    for (size_t e = tid; e < (size_t)m * n; e += nthr)
+        Lw[e] = (float)(A[cm((int)(e % m), (int)(e / m), lda)] * scale);
+    for (int c = tid; c < n; c += nthr) perm[c] = c;
+    __syncthreads();
+    for (int c = wid; c < n; c += nw) {
+        const float v = warp_norm_scaled(Lw + (size_t)c * m, 0, m);
+        if (lane == 0) { vn1[c] = v; vn2[c] = v; }
+    }
+    __syncthreads();
+    const int k = min(m, n);
+    for (int j = 0; j < k; ++j) {
+        // pivot: the first maximum of vn1[j..n)
+        float bv = -1.0f;
+        int bi = n;
+        for (int c = j + tid; c < n; c += nthr) {
+            const float v = vn1[c];
+            if (v > bv) { bv = v; bi = c; }  // increasing c per thread: first maximum kept
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            float b = -1.0f;
+            int p = n;
+            for (int w = 0; w < nw; ++w)
+                if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < p)) { b = s_bv[w]; p = s_bi[w]; }
+            s_p = (p < n) ? p : j;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j) {
+            float* cj = Lw + (size_t)j * m;
+            float* cp = Lw + (size_t)p * m;
+            for (int i = tid; i < m; i += nthr) {
+                const float t = cj[i];
+                cj[i] = cp[i];
+                cp[i] = t;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const int ti = perm[j]; perm[j] = perm[p]; perm[p] = ti;
+                vn1[p] = vn1[j];
+                vn2[p] = vn2[j];
+            }
+        }
+        __syncthreads();
+        // reflector of Lw(j:m, j), stored in place (v(j) = 1 implied)
+        float* colj = Lw + (size_t)j * m;
+        if (wid == 0) {
+            const float tailn = warp_norm_scaled(colj, j + 1, m);
+            float tj = 0.0f, den = 1.0f;
+            if (tailn != 0.0f) {
+                const float alpha = colj[j];
+                const float nrm = warp_norm_scaled(colj, j, m);
+                const float beta = (alpha >= 0.0f) ? -nrm : nrm;
+                tj = (beta - alpha) / beta;
+                den = alpha - beta;
+                __syncwarp();
+                if (lane == 0) colj[j] = beta;
+            }
+            if (lane == 0) { s_tj = tj; s_den = den; }
+        }
+        __syncthreads();
+        const float tj = s_tj, den = s_den;
+        if (tj != 0.0f)
+            for (int i = j + 1 + tid; i < m; i += nthr) colj[i] = colj[i] / den;
+        __syncthreads();
+        // apply H_j to the later columns (one warp per column), downdate their norms
+        for (int c = j + 1 + wid; c < n; c += nw) {
+            float* col = Lw + (size_t)c * m;
+            if (tj != 0.0f) {
+                float w = 0.0f;
+                for (int i = j + 1 + lane; i < m; i += 32) w = fmaf(colj[i], col[i], w);
+                w = warp_sum(w);
+                w = tj * (col[j] + w);
+                __syncwarp();
+                if (lane == 0) col[j] -= w;
+                for (int i = j + 1 + lane; i < m; i += 32) col[i] = fmaf(-w, colj[i], col[i]);
+                __syncwarp();
+            }
+            const float v1 = vn1[c];
+            if (v1 != 0.0f) {
+                const float r = fabsf(col[j]) / v1;
+                float q = 1.0f - r * r;
+                q = q < 0.0f ? 0.0f : q;
+                const float ratio = v1 / vn2[c];
+                if (q * ratio * ratio <= tol3z) {
+                    const float v = warp_norm_scaled(col, j + 1, m);
+                    if (lane == 0) { vn1[c] = v; vn2[c] = v; }
+                } else if (lane == 0) {
+                    vn1[c] = v1 * sqrtf(q);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
+// The binary32 stage of one matrix with blocks of WL columns (one CTA, visits in order).
+template <int WL>
+__device__ bool low_sweeps(const SweepDims& D0, float* Xl, DevState* st, VisitShared<float, WL>& sm)
+{
+    SweepDims D = D0;
+    D.w = WL;
+    const int nb = (D.n + WL - 1) / WL;
+    D.k = max(2, nb + (nb & 1));
+    const Group g1{0, 1, st};
+    bool conv = false;
+    if (D.n <= (int)blockDim.x)
+        jacobi_sweeps<float, false, WL, 1>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm, &conv);
+    else
+        jacobi_sweeps<float, false, WL, 2>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm, &conv);
+    return conv;
+}
+
+// The binary64 refinement with V of one matrix with blocks of WW columns.
+template <int WW>
+__device__ bool work_sweeps(const SweepDims& D0, double* Y, double* Vacc, DevState* st, VisitShared<double, WW>& sm)
+{
+    SweepDims D = D0;
+    D.w = WW;
+    const int nb = (D.n + WW - 1) / WW;
+    D.k = max(2, nb + (nb & 1));
+    const Group g1{0, 1, st};
+    bool conv = false;
+    if (D.n <= (int)blockDim.x)
+        jacobi_sweeps<double, true, WW, 1>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm, &conv);
+    else
+        jacobi_sweeps<double, true, WW, 2>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm, &conv);
+    return conv;
+}
+
 // The whole of Algorithm 4 for one matrix by one CTA. Returns the status bits.
 __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* smem)
 {
@@ -230,8 +433,11 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
     const int tid = threadIdx.x, nthr = blockDim.x;
     __shared__ int s_flag;
     __shared__ int s_status;
-    __shared__ VisitShared<float, kBatchWLow> sm_low;
-    __shared__ VisitShared<double, kBatchWWork> sm_work;
+    __shared__ VisitShared<float, 8> sm_low8;
+    __shared__ VisitShared<float, 16> sm_low16;
+    __shared__ VisitShared<double, 4> sm_work4;
+    __shared__ VisitShared<double, 8> sm_work8;
+    const int var = B.variant[size_class(n)];
 
     // state block: barrier words unused (group of one CTA), counters zeroed
     for (size_t i = tid; i < sizeof(DevState) / 4; i += nthr) ((int*)st)[i] = 0;
@@ -254,14 +460,28 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         return MPJSVD_STATUS_NONFINITE;
     }
 
-    // ---- [3.1] QRCP of A (one CTA)
+    // ---- [3.1] RRQR of A (one CTA): Alg. 5 (binary32 pivot order, then the binary64 QR of
+    // A P) or Businger-Golub in binary64
     Group g1{0, 1, st};
-    hh_qr<true>(g1, m, n, Wq, m, tau, perm, (double*)smem);
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        const double* src = Wq + cm(0, perm[j], m);
-        double* dst = WqL + cm(0, j, m);
-        for (int i = tid; i < m; i += nthr) dst[i] = src[i];
+    if (P.qrcp == MPJSVD_QRCP_MIXED) {
+        cta_qrcp_pivots_f32(m, n, A, lda, (float*)(slot + L.wl), (float*)(slot + L.vn),
+                            (float*)(slot + L.vn) + B.max_n, perm);
+        for (int j = 0; j < n; ++j) {
+            const double* src = Wq + cm(0, perm[j], m);
+            double* dst = WqL + cm(0, j, m);
+            for (int i = tid; i < m; i += nthr) dst[i] = src[i];
+        }
+        __syncthreads();
+        hh_qr<false>(g1, m, n, WqL, m, tau, perm2, (double*)smem);
+        __syncthreads();
+    } else {
+        hh_qr<true>(g1, m, n, Wq, m, tau, perm, (double*)smem);
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const double* src = Wq + cm(0, perm[j], m);
+            double* dst = WqL + cm(0, j, m);
+            for (int i = tid; i < m; i += nthr) dst[i] = src[i];
+        }
     }
     __syncthreads();  // X below reads entries other threads gathered
     for (size_t e = tid; e < nn; e += nthr) {
@@ -339,9 +559,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         for (size_t e = tid; e < nn; e += nthr) Xl[e] = (float)X[e];
         __syncthreads();
         SweepDims D;
-        D.n = n; D.mX = n; D.ldX = n; D.nV = 0; D.ldV = n; D.w = kBatchWLow;
-        int nb = (n + kBatchWLow - 1) / kBatchWLow;
-        D.k = max(2, nb + (nb & 1));
+        D.n = n; D.mX = n; D.ldX = n; D.nV = 0; D.ldV = n;
         D.maxsweep = min(P.maxsweep, 64);
         D.stop = P.stop;
         D.tol = sqrt((double)n) * 5.9604644775390625e-08;
@@ -351,13 +569,8 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         D.ver = nullptr;  // one CTA per matrix: visits run in order, no hand-off
         for (int j = tid; j < n; j += nthr) dscf[j] = 1.0f;
         __syncthreads();
-        bool conv = false;
-        if (n <= nthr)
-            jacobi_sweeps<float, false, kBatchWLow, 1>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm_low,
-                                                          &conv);
-        else
-            jacobi_sweeps<float, false, kBatchWLow, 2>(g1, D, Xl, nullptr, st->rot_sweep[0], st->mx_cos[0], st->mx_tan[0], sm_low,
-                                                          &conv);
+        const bool conv = (var_wlow(var) == 16) ? low_sweeps<16>(D, Xl, st, sm_low16)
+                                                : low_sweeps<8>(D, Xl, st, sm_low8);
         fold_scales_cols<float>(g1, n, n, Xl, n, 0, nullptr, n, dscf);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();
@@ -398,9 +611,7 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
     // ---- [3.4] binary64 refinement with V
     {
         SweepDims D;
-        D.n = n; D.mX = n; D.ldX = n; D.nV = n; D.ldV = n; D.w = kBatchWWork;
-        int nb = (n + kBatchWWork - 1) / kBatchWWork;
-        D.k = max(2, nb + (nb & 1));
+        D.n = n; D.mX = n; D.ldX = n; D.nV = n; D.ldV = n;
         D.maxsweep = min(P.maxsweep, 64);
         D.stop = P.stop;
         D.tol = (B.tol > 0.0) ? B.tol : sqrt((double)n) * 1.1102230246251565e-16;
@@ -410,13 +621,8 @@ __device__ int svd_one(const BatchArgs& B, int mat, char* slot, unsigned char* s
         D.ver = nullptr;  // one CTA per matrix: visits run in order, no hand-off
         for (int j = tid; j < n; j += nthr) dscd[j] = 1.0;
         __syncthreads();
-        bool conv = false;
-        if (n <= nthr)
-            jacobi_sweeps<double, true, kBatchWWork, 1>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm_work,
-                                                            &conv);
-        else
-            jacobi_sweeps<double, true, kBatchWWork, 2>(g1, D, Y, Vacc, st->rot_sweep[1], st->mx_cos[1], st->mx_tan[1], sm_work,
-                                                            &conv);
+        const bool conv = (var_wwork(var) == 8) ? work_sweeps<8>(D, Y, Vacc, st, sm_work8)
+                                                : work_sweeps<4>(D, Y, Vacc, st, sm_work4);
         fold_scales_cols<double>(g1, n, n, Y, n, n, Vacc, n, dscd);
         if (!conv) s_status |= MPJSVD_STATUS_NOT_CONVERGED;
         __syncthreads();
@@ -444,13 +650,156 @@ __global__ void k_batched(BatchArgs B)
         __syncthreads();
         if (idx >= B.batch) break;
         int mat = B.order[idx];
+        const int mi = B.m[mat], ni = B.n[mat], li = B.lda[mat];
+        if (ni < 1 || ni > B.max_n || mi < ni || mi > B.max_m || li < mi) {
+            // sizes outside the call's stated bounds (device-array call): reported, not run
+            if (threadIdx.x == 0) B.info[mat] = -1;
+            __syncthreads();
+            continue;
+        }
         int status = svd_one(B, mat, slot, smem_raw);
         if (threadIdx.x == 0) B.info[mat] = status;
         __syncthreads();
     }
 }
 
+// Largest first: order[rank] = i with rank by n_i^2 m_i descending (stable in i); matrices
+// with sizes outside the bounds rank last (the kernel reports them with info = -1).
+__global__ void k_batch_order(int batch, int max_m, int max_n, const int* m, const int* n, const int* lda,
+                              int* order)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
+        auto key = [&](int j) {
+            const int mj = m[j], nj = n[j];
+            const bool ok = nj >= 1 && nj <= max_n && mj >= nj && mj <= max_m && lda[j] >= mj;
+            return ok ? (double)nj * nj * mj : -1.0;
+        };
+        const double ki = key(i);
+        int r = 0;
+        for (int j = 0; j < batch; ++j) {
+            const double kj = key(j);
+            r += (kj > ki) || (kj == ki && j < i);
+        }
+        order[r] = i;
+    }
+}
+
 static size_t batched_smem(int max_m, int max_n) { return hh_qr_smem_bytes(max_m, max_n, 1); }
+
+// Workspace, launch configuration and the common arguments of a batched launch.
+static int batched_setup(mpjsvd_ctx* h, int batch, int max_m, int max_n, BatchArgs& B, int& grid,
+                         size_t& smem, int*& meta)
+{
+    smem = batched_smem(max_m, max_n);
+    cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("batched smem attribute", e);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, kBatchThreads, smem);
+    if (e != cudaSuccess) return cuda_fail("batched occupancy", e);
+    if (occ < 1) return cuda_fail("batched occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
+    grid = std::min(batch, occ * h->num_sms);
+    SlotLayout L = slot_layout(max_m, max_n);
+    const size_t slot_bytes = al256(L.total);
+    const size_t meta_bytes = al256(sizeof(int) * (size_t)batch * 4) + 256;
+    int rc = ensure_buffer(&h->bws, &h->bws_bytes, meta_bytes + slot_bytes * (size_t)grid);
+    if (rc) return rc;
+    char* base = (char*)h->bws;
+    meta = (int*)base;
+    B.queue = (unsigned int*)(base + al256(sizeof(int) * (size_t)batch * 4));
+    B.slots = base + meta_bytes;
+    B.slot_bytes = slot_bytes;
+    B.max_m = max_m;
+    B.max_n = max_n;
+    B.P = h->params;
+    for (int c = 0; c < kBatchClasses; ++c)
+        B.variant[c] = h->params.block_w != 0 ? kBatchDefaultVariant
+                                              : (h->bt_tuned[c] ? h->bt_variant[c] : kBatchDefaultVariant);
+    return 0;
+}
+
+static int batched_launch(mpjsvd_ctx* h, const BatchArgs& B, int grid, size_t smem)
+{
+    cudaError_t e = cudaMemsetAsync(B.queue, 0, sizeof(unsigned int), h->stream);
+    if (e != cudaSuccess) return cuda_fail("batched queue reset", e);
+    k_batched<<<grid, kBatchThreads, smem, h->stream>>>(B);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("batched launch", e);
+    ++h->launch_count;
+    return 0;
+}
+
+// Autotuner: for every size class of n present in the batch and not tuned yet on this handle,
+// run each kernel variant (block widths of the two stages) on a sample of that class's matrices
+// (up to one per CTA slot of a wave), timed with CUDA events, and keep the fastest. The picks
+// stay in the handle. Host-synchronizing; runs in the host-array call only.
+static int batched_tune(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,
+                        const double* const* A, double* const* U, double* const* S, double* const* V,
+                        double tol, int* info, int max_m, int max_n)
+{
+    if (h->params.block_w != 0) return 0;
+    std::vector<int> cls[kBatchClasses];
+    for (int i = 0; i < batch; ++i) cls[size_class(n[i])].push_back(i);
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return cuda_fail("tune event", cudaErrorUnknown);
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail("tune event", cudaErrorUnknown);
+    }
+    int rc = 0;
+    for (int c = 0; c < kBatchClasses && rc == 0; ++c) {
+        if (h->bt_tuned[c] || cls[c].empty()) continue;
+        // a sample: the class's largest matrices first (the cost the launch is bound by)
+        std::vector<int> smp = cls[c];
+        std::stable_sort(smp.begin(), smp.end(), [&](int a, int b) {
+            return (double)n[a] * n[a] * m[a] > (double)n[b] * n[b] * m[b];
+        });
+        BatchArgs B;
+        int grid = 0;
+        size_t smem = 0;
+        int* meta = nullptr;
+        if ((rc = batched_setup(h, batch, max_m, max_n, B, grid, smem, meta))) break;
+        const int ns = std::min((int)smp.size(), grid);
+        smp.resize(ns);
+        std::vector<int> host(4 * (size_t)batch, 0);
+        for (int i = 0; i < ns; ++i) host[i] = smp[i];
+        for (int i = 0; i < batch; ++i) {
+            host[batch + i] = m[i];
+            host[2 * batch + i] = n[i];
+            host[3 * batch + i] = lda[i];
+        }
+        cudaError_t e = cudaMemcpyAsync(meta, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) { rc = cuda_fail("tune metadata", e); break; }
+        B.batch = ns;
+        B.order = meta;
+        B.m = meta + batch;
+        B.n = meta + 2 * batch;
+        B.lda = meta + 3 * batch;
+        B.A = A; B.U = U; B.S = S; B.V = V; B.info = info; B.tol = tol;
+        float best = 0.0f;
+        int best_v = kBatchDefaultVariant;
+        for (int v = 0; v < kBatchVariants && rc == 0; ++v) {
+            for (int cc = 0; cc < kBatchClasses; ++cc) B.variant[cc] = v;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && rc == 0; ++rep) {  // the second run is timed
+                cudaEventRecord(ev[0], h->stream);
+                rc = batched_launch(h, B, std::min(grid, ns), smem);
+                cudaEventRecord(ev[1], h->stream);
+                if (rc == 0 && cudaEventSynchronize(ev[1]) == cudaSuccess)
+                    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            }
+            if (rc == 0 && (v == 0 || ms < best)) { best = ms; best_v = v; }
+        }
+        if (rc == 0) {
+            h->bt_variant[c] = best_v;
+            h->bt_ms[c] = best;
+            h->bt_tuned[c] = true;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return rc;
+}
 
 int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int* lda,
                 const double* const* A, double* const* U, double* const* S, double* const* V,
@@ -461,28 +810,20 @@ int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int*
         max_m = std::max(max_m, m[i]);
         max_n = std::max(max_n, n[i]);
     }
+    h->launch_count = 0;
+    int rc = batched_tune(h, batch, m, n, lda, A, U, S, V, tol, info, max_m, max_n);
+    if (rc) return rc;
     // largest first
     std::vector<int> order(batch);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (double)n[a] * n[a] * m[a] > (double)n[b] * n[b] * m[b];
     });
-    size_t smem = batched_smem(max_m, max_n);
-    cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail("batched smem attribute", e);
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, kBatchThreads, smem);
-    if (e != cudaSuccess) return cuda_fail("batched occupancy", e);
-    if (occ < 1) return cuda_fail("batched occupancy (0 blocks fit)", cudaErrorInvalidConfiguration);
-    int grid = std::min(batch, occ * h->num_sms);
-    SlotLayout L = slot_layout(max_m, max_n);
-    size_t slot_bytes = al256(L.total);
-    size_t meta = al256(sizeof(int) * (size_t)batch * 4) + 256;
-    int rc = ensure_buffer(&h->bws, &h->bws_bytes, meta + slot_bytes * (size_t)grid);
-    if (rc) return rc;
-    char* base = (char*)h->bws;
-    int* d_meta = (int*)base;  // order | m | n | lda
-    unsigned int* queue = (unsigned int*)(base + al256(sizeof(int) * (size_t)batch * 4));
+    BatchArgs B;
+    int grid = 0;
+    size_t smem = 0;
+    int* d_meta = nullptr;
+    if ((rc = batched_setup(h, batch, max_m, max_n, B, grid, smem, d_meta))) return rc;
     std::vector<int> host(4 * (size_t)batch);
     for (int i = 0; i < batch; ++i) {
         host[i] = order[i];
@@ -492,33 +833,54 @@ int svd_batched(mpjsvd_ctx* h, int batch, const int* m, const int* n, const int*
     }
     // from pageable memory: the copy is staged before cudaMemcpyAsync returns, so the host
     // vector may go out of scope afterwards
-    e = cudaMemcpyAsync(d_meta, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(d_meta, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice,
+                                    h->stream);
     if (e != cudaSuccess) return cuda_fail("batched metadata copy", e);
-    e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), h->stream);
-    if (e != cudaSuccess) return cuda_fail("batched queue reset", e);
-    BatchArgs B;
     B.batch = batch;
     B.order = d_meta;
     B.m = d_meta + batch;
     B.n = d_meta + 2 * batch;
     B.lda = d_meta + 3 * batch;
-    B.A = A;
-    B.U = U;
-    B.S = S;
-    B.V = V;
-    B.info = info;
-    B.queue = queue;
-    B.slots = base + meta;
-    B.slot_bytes = slot_bytes;
-    B.max_m = max_m;
-    B.max_n = max_n;
-    B.P = h->params;
-    B.tol = tol;
-    k_batched<<<grid, kBatchThreads, smem, h->stream>>>(B);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail("batched launch", e);
-    h->launch_count = 1;
-    return 0;
+    B.A = A; B.U = U; B.S = S; B.V = V; B.info = info; B.tol = tol;
+    h->launch_count = 0;
+    return batched_launch(h, B, grid, smem);
+}
+
+// Sizes in device memory (capturable in a CUDA graph: no host copy, no allocation once the
+// workspace for (batch, max_m, max_n) exists): the order is computed on the device.
+int svd_batched_dev(mpjsvd_ctx* h, int batch, int max_m, int max_n, const int* m, const int* n, const int* lda,
+                    const double* const* A, double* const* U, double* const* S, double* const* V, double tol,
+                    int* info)
+{
+    BatchArgs B;
+    int grid = 0;
+    size_t smem = 0;
+    int* d_meta = nullptr;
+    h->launch_count = 0;
+    int rc = batched_setup(h, batch, max_m, max_n, B, grid, smem, d_meta);
+    if (rc) return rc;
+    k_batch_order<<<std::max(1, std::min(h->num_sms * 4, (batch + 255) / 256)), 256, 0, h->stream>>>(
+        batch, max_m, max_n, m, n, lda, d_meta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("batched order", e);
+    ++h->launch_count;
+    B.batch = batch;
+    B.order = d_meta;
+    B.m = m;
+    B.n = n;
+    B.lda = lda;
+    B.A = A; B.U = U; B.S = S; B.V = V; B.info = info; B.tol = tol;
+    return batched_launch(h, B, grid, smem);
+}
+
+void batched_tuning(const mpjsvd_ctx* h, int* wl, int* ww, float* ms)
+{
+    for (int c = 0; c < kBatchClasses; ++c) {
+        const int v = h->bt_tuned[c] ? h->bt_variant[c] : kBatchDefaultVariant;
+        if (wl) wl[c] = h->bt_tuned[c] ? var_wlow(v) : 0;
+        if (ww) ww[c] = h->bt_tuned[c] ? var_wwork(v) : 0;
+        if (ms) ms[c] = h->bt_tuned[c] ? h->bt_ms[c] : 0.0f;
+    }
 }
 
 }  // namespace mpj

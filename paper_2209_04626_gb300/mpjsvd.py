@@ -30,7 +30,8 @@ EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsv
            "mpjsvd_svd", "mpjsvd_svd_batched", "mpjsvd_svd_backward", "mpjsvd_get_stats",
            "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
            "mpjsvd_apply_q", "mpjsvd_geqp3", "mpjsvd_selftest_timeout",
-           "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak", "mpjsvd_tc_block_f32"]
+           "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak", "mpjsvd_tc_block_f32",
+           "mpjsvd_svd_batched_dev", "mpjsvd_get_batched_tuning"]
 
 
 class Params(ctypes.Structure):
@@ -94,6 +95,8 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_selftest_timeout.argtypes = [_vp]
     L.mpjsvd_measure_fp64_peak.argtypes = [_vp, ctypes.POINTER(_d)]
     L.mpjsvd_tc_block_f32.argtypes = [_vp, _i, _vp, _i, _vp, _vp]
+    L.mpjsvd_svd_batched_dev.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp]
+    L.mpjsvd_get_batched_tuning.argtypes = [_vp, _vp, _vp, _vp]
     L.mpjsvd_svd_backward_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _d, _vp]
     _lib = L
@@ -167,6 +170,20 @@ def mpjsvd_svd_backward_batched(h, batch, m_host, n_host, U_ptrs, S_ptrs, V_ptrs
     return load_library().mpjsvd_svd_backward_batched(
         h, batch, _vp(m_host), _vp(n_host), _vp(U_ptrs), _vp(S_ptrs), _vp(V_ptrs), _vp(gU_ptrs),
         _vp(gS_ptrs), _vp(gV_ptrs), _vp(gA_ptrs), gap_tol, _vp(flags_ptr))
+
+
+def mpjsvd_svd_batched_dev(h, batch, max_m, max_n, m_ptr, n_ptr, lda_ptr, A_ptrs, U_ptrs, S_ptrs,
+                           V_ptrs, tol, info_ptr):
+    return load_library().mpjsvd_svd_batched_dev(h, batch, max_m, max_n, _vp(m_ptr), _vp(n_ptr),
+                                                 _vp(lda_ptr), _vp(A_ptrs), _vp(U_ptrs), _vp(S_ptrs),
+                                                 _vp(V_ptrs), tol, _vp(info_ptr))
+
+
+def mpjsvd_get_batched_tuning(h):
+    """Per size class of n (<= 32, 64, 128, 256, 512): (w_low, w_work, sample ms), 0 if untuned."""
+    wl, ww, ms = (ctypes.c_int * 5)(), (ctypes.c_int * 5)(), (ctypes.c_float * 5)()
+    _check(load_library().mpjsvd_get_batched_tuning(h, wl, ww, ms), "mpjsvd_get_batched_tuning")
+    return [(wl[i], ww[i], ms[i]) for i in range(5)]
 
 
 def mpjsvd_get_stats(h):

@@ -103,6 +103,6 @@ def test_batched_4096_full():
         U, S, V = Us[i].cpu().numpy(), Ss[i].cpu().numpy(), Vs[i].cpu().numpy()
         check_factorization(A, U, S, V)
         check_sign_rule(V)
-        _, So, _, _ = oracle.svd(A, mode="mixed", qrcp=0)
+        _, So, _, _ = oracle.svd(A, mode="mixed", qrcp=1)
         sigma_gate(A, S, So)
     h.close()
