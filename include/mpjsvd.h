@@ -20,6 +20,16 @@
  *      assembled from the factors (Alg. 4, last line).
  * Every stage runs as hand-written CUDA kernels on the handle's stream.
  *
+ * Departures from the plain statement of the method, each with the same limit:
+ *   - the binary64 stage evaluates each rotation's tangent in binary32 from the binary64
+ *     alpha, beta, gamma (scaled by a power of two) and its cosine in binary64 for that
+ *     tangent: every rotation is orthogonal to binary64 precision and only how completely a
+ *     pair is annihilated (to about 2^-23 of gamma) depends on the binary32 tangent; the
+ *     dot products, the rotation test and the convergence test are binary64;
+ *   - the binary32 stage at large n (params.low_kernel) runs in blocked form on the tensor
+ *     cores: each visit's rotations are computed from the block pair's Gram matrix (TF32 with a
+ *     3-term split, binary32 accumulation) instead of from the columns.
+ *
  * Conventions for every entry point:
  *   - Matrices are column-major FP64 (element (i, j) at ptr[j * ld + i]).
  *   - Matrix pointers are DEVICE pointers owned by the caller; the library never frees
@@ -75,6 +85,13 @@ extern "C" {
                                 matrices and rotation application by TF32x3 tcgen05 MMAs */
 #define MPJSVD_LOWK_REG 2    /* register-resident level-1 visits (no tensor cores) */
 
+/* params.gemm_kernel: the n x n x n binary64 products (the switch of Section 3.3, the safeguard
+ * and the V from QR of Section 3.4). */
+#define MPJSVD_GEMMK_AUTO 0  /* tensor cores from n = 1024 on */
+#define MPJSVD_GEMMK_TC 1    /* bf16 tensor cores by error-free operand splitting (see
+                                mpjsvd_dgemm_tc) */
+#define MPJSVD_GEMMK_F64 2   /* the FP64 pipe (register-blocked SIMT kernel) */
+
 /* params.switch_method: the precision switch of Section 3.3. */
 #define MPJSVD_SWITCH_U 0    /* B = X^T U_low, B = Q R2, Y = X Q (the method the paper prefers;
                                 default) */
@@ -117,6 +134,7 @@ typedef struct {
                              X^T U_X and one more Alg. 1 with V accumulated from that Q
                              (Section 3.4); 0 (default): V accumulated through the refinement */
     int switch_method;    /* MPJSVD_SWITCH_* */
+    int gemm_kernel;      /* MPJSVD_GEMMK_* */
     double y_tol;         /* > 0: the Y1/Y2 safeguard of Section 3.4 with this cosine
                              threshold (Y2 = the columns of Y from the first one whose largest
                              cosine with an earlier column exceeds y_tol: Alg. 1 on Y2, one pass
@@ -314,6 +332,21 @@ int mpjsvd_apply_q(mpjsvd_handle h, int m, int ncols, int k, const double* A, in
  *   m : rows of Z, 1 <= m; Z: device, m x 128 binary32, leading dimension ldz >= m
  * Stream-ordered on the handle's stream; one CTA. */
 int mpjsvd_tc_block_f32(mpjsvd_handle h, int m, float* Z, int ldz, float* G, const float* W);
+
+/* C = op(A) B in binary64 on the bf16 tensor cores (the products of the precision switch of
+ * Section 3.3 as a standalone call): each row of op(A) and each column of B is scaled by a
+ * power of two and split into 8 slices of 7 bits (bf16 values); the slice products of the
+ * weight classes that matter are accumulated exactly in binary32 on the tensor cores
+ * (tcgen05.mma) over chunks of 512 k and added in binary64 (the Ozaki scheme); products of
+ * integers that are exact in binary64 come out exact. Error per
+ * entry: about 2^-52 K max_k |op(A)_ik| max_k |B_kj|, the bound of a binary64 GEMM with the
+ * row and column maxima in place of the entries.
+ *   op(A) = A (transA = 0; A: M x K, lda >= M) or A^T (transA = 1; A: K x M, lda >= K)
+ *   B : K x N, ldb >= K;  C : M x N, ldc >= M (overwritten). Device pointers, column-major.
+ * Stream-ordered on the handle's stream; uses the handle's workspace (about 4 K (M + N) bytes
+ * for the split operands). */
+int mpjsvd_dgemm_tc(mpjsvd_handle h, int M, int N, int K, const double* A, int lda, int transA,
+                    const double* B, int ldb, double* C, int ldc);
 
 /* Measurement utility (not part of the paper): the FP64 FMA throughput of the current GPU in
  * TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on every SM, timed with

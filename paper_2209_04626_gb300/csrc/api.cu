@@ -89,6 +89,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->low_kernel = MPJSVD_LOWK_AUTO;
     p->v_by_qr = 0;
     p->switch_method = MPJSVD_SWITCH_U;
+    p->gemm_kernel = MPJSVD_GEMMK_AUTO;
     p->y_tol = 0.0;
     return 0;
 }
@@ -106,6 +107,7 @@ static int check_params(const mpjsvd_params* p)
     if (p->low_kernel < 0 || p->low_kernel > 2) return 1;
     if (p->v_by_qr < 0 || p->v_by_qr > 1) return 1;
     if (p->switch_method < 0 || p->switch_method > 1) return 1;
+    if (p->gemm_kernel < 0 || p->gemm_kernel > 2) return 1;
     if (!(p->y_tol >= 0.0 && p->y_tol < 1.0)) return 1;
     return 0;
 }

@@ -112,6 +112,11 @@ int svd_batched_dev(mpjsvd_ctx* h, int batch, int max_m, int max_n, const int* m
                     int* info);
 void batched_tuning(const mpjsvd_ctx* h, int* w_low, int* w_work, float* ms);
 
+// binary64 products on the bf16 tensor cores by operand splitting (ozaki.cu)
+struct GemmArgs;
+size_t ozaki_ws_bytes(int M, int N, int K);
+int ozaki_dgemm(mpjsvd_ctx* h, const GemmArgs& g, void* ws, const int* gate, int want, DevState* st);
+
 // adjoint (adjoint.cu)
 int svd_backward(mpjsvd_ctx* h, int m, int n, const double* U, const double* S, const double* V,
                  const double* gU, const double* gS, const double* gV, double* gA, double gap_tol,

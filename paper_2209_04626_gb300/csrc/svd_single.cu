@@ -26,6 +26,7 @@ namespace mpj {
 
 constexpr int kWmaxLow = 16;   // widest binary32 block (register-resident visits)
 constexpr int kLowTcMinN = 5120;  // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
+constexpr int kGemmTcMinN = 1024; // MPJSVD_GEMMK_AUTO: tensor-core binary64 GEMMs from this n on
 constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
@@ -508,18 +509,18 @@ __global__ void k_finalize(int m, int n, const double* __restrict__ Y, const dou
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct SingleLayout {
-    size_t off[32];  // >= L_COUNT (static_assert below)
+    size_t off[40];  // >= L_COUNT (static_assert below)
     size_t total;
 };
 
 enum {
     L_WQ, L_WQL, L_W0, L_TAU0, L_TAU, L_PERM, L_IPOS, L_VN1, L_VN2, L_X, L_XL, L_CN, L_G,
     L_SIGL, L_ORD, L_UL, L_BQ, L_TAU2, L_Y, L_VACC, L_SIG, L_ORD2, L_BITS, L_PERM2, L_DSC,
-    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_WY, L_LQ, L_TAUQ, L_COUNT
+    L_ALPH, L_BCAST, L_FLAGS, L_VER, L_WY, L_LQ, L_TAUQ, L_OZ, L_COUNT
 };
-static_assert(L_COUNT <= 32, "SingleLayout::off is too small");
+static_assert(L_COUNT <= 40, "SingleLayout::off is too small");
 
-static SingleLayout single_layout(int m, int n, bool qr_first, bool lq)
+static SingleLayout single_layout(int m, int n, bool qr_first, bool lq, bool oz)
 {
     size_t nn = (size_t)n * n;
     int mq = qr_first ? n : m;
@@ -556,6 +557,7 @@ static SingleLayout single_layout(int m, int n, bool qr_first, bool lq)
     sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n, m);
     sz[L_LQ] = lq ? sizeof(double) * nn : 0;   // the QR of R^T (second preconditioning)
     sz[L_TAUQ] = lq ? sizeof(double) * n : 0;
+    sz[L_OZ] = oz ? ozaki_ws_bytes(n, n, n) : 0;  // split operands of the tensor-core GEMMs
     // The QRCP's broadcast slots are live only during the QR preconditioning; the buffers
     // from X up to V_acc are first written after it, so the slots share their memory when
     // they fit (L_BITS, zeroed at the start of a call, is not in that span).
@@ -696,7 +698,11 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     const mpjsvd_params& P = h->params;
     const bool qr_first = P.qr_first && m > n;
     const bool lq = P.precond >= MPJSVD_PRECOND_L;
-    SingleLayout L = single_layout(m, n, qr_first, lq);
+    // the n x n x n binary64 GEMMs (switch, safeguard, V from QR): on the tensor cores by
+    // operand splitting, or on the FP64 pipe
+    const bool oz = P.gemm_kernel == MPJSVD_GEMMK_TC ||
+                    (P.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN);
+    SingleLayout L = single_layout(m, n, qr_first, lq, oz);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;
     char* base = (char*)h->ws;
@@ -729,6 +735,10 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     unsigned* ver = (unsigned*)ptr(L_VER);
     double* wy = (double*)ptr(L_WY);
     double* Lq = (double*)ptr(L_LQ);
+    void* ozws = ptr(L_OZ);
+    auto gemm64 = [&](const GemmArgs& ga, const int* gate, int want) {
+        return oz ? ozaki_dgemm(h, ga, ozws, gate, want, (DevState*)h->dstate) : launch_gemm_d(h, ga, gate, want);
+    };
     double* tauq = (double*)ptr(L_TAUQ);
     // n x n factorizations are always blocked (every n <= 12288 has a panel width); the QRCP's
     // broadcast slots may alias the stage buffers, so no unblocked kernel runs after it
@@ -855,7 +865,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
             g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
             g2.klo_from_row = x_upper;
             g2.khi_from_row = x_lower;
-            if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
+            if ((rc = gemm64(g2, &st->gate_low, 1))) return rc;
         } else {
             if (low_tc) {
                 if ((rc = launch_bsweeps_tf32(h, Dl, Xl, st, 0, 1))) return rc;
@@ -873,7 +883,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
             g.B = Ul; g.ldb = n; g.C = Bq; g.ldc = n;
             g.klo_from_row = x_lower;  // X^T upper when X lower
             g.khi_from_row = x_upper;
-            if ((rc = launch_gemm_d(h, g, &st->gate_low, 1))) return rc;
+            if ((rc = gemm64(g, &st->gate_low, 1))) return rc;
             if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
             k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
             if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
@@ -883,7 +893,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
             g2.B = Vacc; g2.ldb = n; g2.C = Y; g2.ldc = n;
             g2.klo_from_row = x_upper;  // X upper: X(i, k) = 0 for k < i
             g2.khi_from_row = x_lower;  // X lower: X(i, k) = 0 for k > i
-            if ((rc = launch_gemm_d(h, g2, &st->gate_low, 1))) return rc;
+            if ((rc = gemm64(g2, &st->gate_low, 1))) return rc;
         }
     } else {
         record(h, 3);
@@ -913,7 +923,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         gy.A = Y; gy.lda = n; gy.transA = true;
         gy.B = Y; gy.ldb = n; gy.C = Bq; gy.ldc = n;
         gy.klo_from_row = gy.khi_from_row = false;
-        if ((rc = launch_gemm_d(h, gy, nullptr, 0))) return rc;
+        if ((rc = gemm64(gy, nullptr, 0))) return rc;
         k_y_partition_init<<<1, 1, 0, s>>>(n, st); ++h->launch_count;  // also records n
         k_y_partition<<<std::max(1, std::min(egrid, (n * 32 + T256 - 1) / T256)), T256, 0, s>>>(
             n, Bq, cn, P.y_tol, st); ++h->launch_count;
@@ -944,7 +954,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g3.B = Ul; g3.ldb = n; g3.C = Bq; g3.ldc = n;
         g3.klo_from_row = x_lower;
         g3.khi_from_row = x_upper;
-        if ((rc = launch_gemm_d(h, g3, nullptr, 0))) return rc;
+        if ((rc = gemm64(g3, nullptr, 0))) return rc;
         if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, -1))) return rc;
         k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, -1); ++h->launch_count;
         if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, -1))) return rc;
@@ -954,7 +964,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g4.B = Vacc; g4.ldb = n; g4.C = Y; g4.ldc = n;
         g4.klo_from_row = x_upper;
         g4.khi_from_row = x_lower;
-        if ((rc = launch_gemm_d(h, g4, nullptr, 0))) return rc;
+        if ((rc = gemm64(g4, nullptr, 0))) return rc;
         if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 2, -1, nullptr))) return rc;
     }
     record(h, 5);
@@ -1130,7 +1140,9 @@ static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double
     // the workspace svd_single will ask for, from the same parameters it reads
     const size_t state_bytes = align256(sizeof(DevState));
     const size_t need = single_layout(m, n, ctx.params.qr_first && m > n,
-                                      ctx.params.precond >= MPJSVD_PRECOND_L).total;
+                                      ctx.params.precond >= MPJSVD_PRECOND_L,
+                                      ctx.params.gemm_kernel == MPJSVD_GEMMK_TC ||
+                                          (ctx.params.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN)).total;
     if (state_bytes + need > kNoAllocBytes)
         return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
                          cudaErrorInvalidValue);

@@ -23,6 +23,7 @@ QRCP = {"mixed": 0, "f64": 1}
 STOP = {"xgesvj": 0, "alg1": 1}
 LOWK = {"auto": 0, "tc": 1, "reg": 2}
 SWITCH = {"u": 0, "v": 1}
+GEMMK = {"auto": 0, "tc": 1, "f64": 2}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -31,7 +32,7 @@ EXPORTS = ["mpjsvd_default_params", "mpjsvd_create", "mpjsvd_set_stream", "mpjsv
            "mpjsvd_destroy", "mpjsvd_last_error", "mpjsvd_svd_noalloc", "mpjsvd_geqrf",
            "mpjsvd_apply_q", "mpjsvd_geqp3", "mpjsvd_selftest_timeout",
            "mpjsvd_svd_backward_batched", "mpjsvd_measure_fp64_peak", "mpjsvd_tc_block_f32",
-           "mpjsvd_svd_batched_dev", "mpjsvd_get_batched_tuning"]
+           "mpjsvd_svd_batched_dev", "mpjsvd_get_batched_tuning", "mpjsvd_dgemm_tc"]
 
 
 class Params(ctypes.Structure):
@@ -41,7 +42,7 @@ class Params(ctypes.Structure):
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
                 ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("low_kernel", ctypes.c_int), ("v_by_qr", ctypes.c_int),
-                ("switch_method", ctypes.c_int), ("y_tol", ctypes.c_double)]
+                ("switch_method", ctypes.c_int), ("gemm_kernel", ctypes.c_int), ("y_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -97,6 +98,7 @@ def load_library(path=LIB_PATH):
     L.mpjsvd_tc_block_f32.argtypes = [_vp, _i, _vp, _i, _vp, _vp]
     L.mpjsvd_svd_batched_dev.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp]
     L.mpjsvd_get_batched_tuning.argtypes = [_vp, _vp, _vp, _vp]
+    L.mpjsvd_dgemm_tc.argtypes = [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _i]
     L.mpjsvd_svd_backward_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _d, _vp]
     _lib = L
@@ -127,6 +129,8 @@ def mpjsvd_default_params(**overrides):
             v = LOWK[v]
         if k == "switch_method" and isinstance(v, str):
             v = SWITCH[v]
+        if k == "gemm_kernel" and isinstance(v, str):
+            v = GEMMK[v]
         setattr(p, k, v)
     return p
 
@@ -184,6 +188,11 @@ def mpjsvd_get_batched_tuning(h):
     wl, ww, ms = (ctypes.c_int * 5)(), (ctypes.c_int * 5)(), (ctypes.c_float * 5)()
     _check(load_library().mpjsvd_get_batched_tuning(h, wl, ww, ms), "mpjsvd_get_batched_tuning")
     return [(wl[i], ww[i], ms[i]) for i in range(5)]
+
+
+def mpjsvd_dgemm_tc(h, M, N, K, A_ptr, lda, transA, B_ptr, ldb, C_ptr, ldc):
+    return load_library().mpjsvd_dgemm_tc(h, M, N, K, _vp(A_ptr), lda, transA, _vp(B_ptr), ldb,
+                                          _vp(C_ptr), ldc)
 
 
 def mpjsvd_get_stats(h):
@@ -278,6 +287,8 @@ class Handle:
                 v = LOWK[v]
             if k == "switch_method" and isinstance(v, str):
                 v = SWITCH[v]
+            if k == "gemm_kernel" and isinstance(v, str):
+                v = GEMMK[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 
