@@ -87,7 +87,7 @@ extern "C" {
 
 /* params.gemm_kernel: the n x n x n binary64 products (the switch of Section 3.3, the safeguard
  * and the V from QR of Section 3.4). */
-#define MPJSVD_GEMMK_AUTO 0  /* tensor cores from n = 1024 on */
+#define MPJSVD_GEMMK_AUTO 0  /* tensor cores for 1024 <= n <= 4096 (where measured faster) */
 #define MPJSVD_GEMMK_TC 1    /* bf16 tensor cores by error-free operand splitting (see
                                 mpjsvd_dgemm_tc) */
 #define MPJSVD_GEMMK_F64 2   /* the FP64 pipe (register-blocked SIMT kernel) */

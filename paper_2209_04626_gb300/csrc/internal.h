@@ -89,7 +89,8 @@ int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, 
               double* C, int ldc, bool ident, double* W, DevState* st, int gate_want);
 // binary32 pivot search of Alg. 5 (qrcp_low.cu); 1 = does not fit, nothing launched
 int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
-                    DevState* st);
+                    size_t bcast_bytes, DevState* st);
+size_t qrcp_low_bcast_bytes(int m, int n, int sms);  // what its global-column variant needs
 
 // standalone calls behind mpjsvd_geqrf / mpjsvd_apply_q (workspace and state of the handle)
 int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau);

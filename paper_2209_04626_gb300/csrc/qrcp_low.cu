@@ -54,15 +54,18 @@ __device__ float norm_scaled(const float* x, int lo, int m, float* red)
     return sqrtf(s) / sc;
 }
 
-__host__ __device__ inline size_t qrcp_low_smem_bytes(int m, int n, int gsize)
+__host__ __device__ inline size_t qrcp_low_smem_bytes(int m, int n, int gsize, bool global_cols = false)
 {
     const int own = (n + gsize - 1) / gsize;
-    return sizeof(float) * ((size_t)own * m + m + 3 * (size_t)own) + sizeof(int) * own;
+    return sizeof(float) * ((global_cols ? 0 : (size_t)own * m) + m + 3 * (size_t)own) + sizeof(int) * own;
 }
 
+// GLOBAL = false: the owned columns in shared memory; GLOBAL = true (columns too long for it):
+// in global memory, gcols + rank * own_max * m (L2 and HBM traffic instead of shared memory).
+template <bool GLOBAL>
 __global__ void __launch_bounds__(kLowThreads)
     k_qrcp_low(int m, int n, const double* __restrict__ A, int lda, int* perm, float* bcast,
-               DevState* st)
+               DevState* st, float* gcols)
 {
     extern __shared__ float lsm[];
     __shared__ float red[kLowBatch * 33];
@@ -71,9 +74,10 @@ __global__ void __launch_bounds__(kLowThreads)
     if (call_failed(st)) return;
     const Group g{(int)blockIdx.x, (int)gridDim.x, st};
     const int own = (n - g.rank + g.size - 1) / g.size;
+    const int own_max = (n + g.size - 1) / g.size;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
-    float* C = lsm;                     // own x m
-    float* vs = C + (size_t)own * m;    // m: the step's column, then its reflector
+    float* C = GLOBAL ? gcols + (size_t)g.rank * own_max * m : lsm;  // own x m
+    float* vs = GLOBAL ? lsm : C + (size_t)own * m;                   // m: the step's column, then its reflector
     float* vn1 = vs + m;
     float* vn2 = vn1 + own;
     float* rowj = vn2 + own;
@@ -641,11 +645,21 @@ static int launch_reg(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int
     return 0;
 }
 
+// Bytes of the broadcast region that the global-column variant needs (slots, then columns).
+size_t qrcp_low_bcast_bytes(int m, int n, int sms)
+{
+    const int grid = std::max(1, std::min(n, std::min(sms, kQrSlotStride)));
+    const size_t slots = ((sizeof(unsigned long long) * 2 * (size_t)grid * ((size_t)m + 4)) + 255) & ~size_t(255);
+    const int own_max = (n + grid - 1) / grid;
+    return slots + sizeof(float) * (size_t)grid * own_max * m;
+}
+
 // Launch the binary32 pivot search: register-resident when a column fits a warp's registers
-// and there is a warp per column, else columns resident in shared memory; returns 1
-// (nothing launched) when neither fits, so the caller takes the binary64 QRCP instead.
+// and there is a warp per column, else columns resident in shared memory, else (long columns)
+// columns in global memory after the broadcast slots in bcast (bcast_bytes in all); returns 1
+// (nothing launched) when none fits, so the caller takes the binary64 QRCP instead.
 int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
-                    DevState* st)
+                    size_t bcast_bytes, DevState* st)
 {
     int rc = 1;
     if (m <= 256) rc = launch_reg<8>(h, m, n, A, lda, perm, bcast, st);
@@ -654,16 +668,28 @@ int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* 
     else if (m <= 2048) rc = launch_reg<64>(h, m, n, A, lda, perm, bcast, st);  // 216 registers
     if (rc <= 0) return rc;
     const int grid = std::max(1, std::min(n, std::min(h->num_sms, kQrSlotStride)));
-    const size_t smem = qrcp_low_smem_bytes(m, n, grid);
-    if (smem > 200 * 1024) return 1;
-    cudaError_t e = cudaFuncSetAttribute(k_qrcp_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    bool global_cols = false;
+    size_t smem = qrcp_low_smem_bytes(m, n, grid);
+    float* gcols = nullptr;
+    if (smem > 200 * 1024) {
+        // slots: 2 parities x grid CTAs x (m + 4) words of 8 bytes; then own_max x m floats per CTA
+        const size_t slots = ((sizeof(unsigned long long) * 2 * (size_t)grid * ((size_t)m + 4)) + 255) & ~size_t(255);
+        const int own_max = (n + grid - 1) / grid;
+        const size_t cols = sizeof(float) * (size_t)grid * own_max * m;
+        smem = qrcp_low_smem_bytes(m, n, grid, true);
+        if (slots + cols > bcast_bytes || smem > 200 * 1024) return 1;
+        gcols = (float*)((char*)bcast + slots);
+        global_cols = true;
+    }
+    void* kern = global_cols ? (void*)k_qrcp_low<true> : (void*)k_qrcp_low<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail("qrcp_low smem attribute", e);
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qrcp_low, kLowThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLowThreads, smem);
     if (e != cudaSuccess) return cuda_fail("qrcp_low occupancy", e);
     if (occ < 1) return 1;
-    void* args[] = {&m, &n, &A, &lda, &perm, &bcast, &st};
-    e = cudaLaunchCooperativeKernel((void*)k_qrcp_low, grid, kLowThreads, args, smem, h->stream);
+    void* args[] = {&m, &n, &A, &lda, &perm, &bcast, &st, &gcols};
+    e = cudaLaunchCooperativeKernel(kern, grid, kLowThreads, args, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail("qrcp_low launch", e);
     ++h->launch_count;
     return 0;

@@ -26,7 +26,12 @@ namespace mpj {
 
 constexpr int kWmaxLow = 16;   // widest binary32 block (register-resident visits)
 constexpr int kLowTcMinN = 5120;  // MPJSVD_LOWK_AUTO: tensor-core binary32 stage from this n on
-constexpr int kGemmTcMinN = 1024; // MPJSVD_GEMMK_AUTO: tensor-core binary64 GEMMs from this n on
+// MPJSVD_GEMMK_AUTO: tensor-core binary64 products for n in [kGemmTcMinN, kGemmTcMaxN]. The
+// split product keeps 56 bits of each row relative to the row's largest entry; on graded inputs
+// the refinement then needs a few % more rotations (2048 x 1024 workload: +2.3%, a net gain of
+// 1.4% of the SVD; 8192 x 8192: +10%, a net loss), so large n stays on the FP64 pipe.
+constexpr int kGemmTcMinN = 1024;
+constexpr int kGemmTcMaxN = 4096;
 constexpr int kWmaxWork = 8;   // widest binary64 block
 constexpr int kQrThreads = 256;
 constexpr int kMaxGroupCtas = kQrSlotStride;  // CTAs of a cooperative QR launch
@@ -551,7 +556,8 @@ static SingleLayout single_layout(int m, int n, bool qr_first, bool lq, bool oz)
     sz[L_PERM2] = sizeof(int) * n;
     sz[L_DSC] = sizeof(double) * n;
     sz[L_ALPH] = sizeof(double) * n;
-    sz[L_BCAST] = sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas);
+    sz[L_BCAST] = std::max(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas),
+                           qrcp_low_bcast_bytes(qr_first ? n : m, n, kMaxGroupCtas));
     sz[L_FLAGS] = sizeof(int) * n;
     sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
     sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n, m);
@@ -701,7 +707,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // the n x n x n binary64 GEMMs (switch, safeguard, V from QR): on the tensor cores by
     // operand splitting, or on the FP64 pipe
     const bool oz = P.gemm_kernel == MPJSVD_GEMMK_TC ||
-                    (P.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN);
+                    (P.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN && n <= kGemmTcMaxN);
     SingleLayout L = single_layout(m, n, qr_first, lq, oz);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;
@@ -781,7 +787,10 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // the binary64 Businger-Golub kernel (reflectors gathered into pivot order afterwards)
     bool mixed_done = false;
     if (P.qrcp == MPJSVD_QRCP_MIXED && bqr_nb(mq) > 0 && mq <= 12480) {
-        rc = launch_qrcp_low(h, mq, n, Wq, mq, perm, (float*)bcast, st);
+        // the broadcast region: its own buffer, or the stage buffers it aliases (X .. V_acc)
+        const size_t bc_bytes = (L.off[L_BCAST] == L.off[L_X]) ? (L.off[L_SIG] - L.off[L_X])
+                                                                : (L.off[L_BCAST + 1] - L.off[L_BCAST]);
+        rc = launch_qrcp_low(h, mq, n, Wq, mq, perm, (float*)bcast, bc_bytes, st);
         if (rc < 0) return rc;
         if (rc == 0) {
             k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
@@ -1009,7 +1018,8 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
 int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, double* tau)
 {
     const size_t sz_tmp = align256(sizeof(double) * (size_t)m * n);
-    const size_t sz_bc = align256(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas));
+    const size_t sz_bc = align256(std::max(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas),
+                                           qrcp_low_bcast_bytes(m, n, kMaxGroupCtas)));
     const size_t sz_wy = align256(sizeof(double) * bqr_wbuf_doubles(n, m));
     const size_t sz_fl = align256(sizeof(int) * (size_t)n);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, sz_tmp + sz_bc + sz_wy + sz_fl);
@@ -1027,7 +1037,7 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
     cudaError_t e;
     bool mixed_done = false;
     if (h->params.qrcp == MPJSVD_QRCP_MIXED && bqr_nb(m) > 0 && m <= 12480) {
-        rc = launch_qrcp_low(h, m, n, A, lda, jpvt, (float*)bcast, st);
+        rc = launch_qrcp_low(h, m, n, A, lda, jpvt, (float*)bcast, sz_bc, st);
         if (rc < 0) return rc;
         if (rc == 0) {
             k_gather_cols<<<std::min(n, egrid), 256, 0, s>>>(m, n, A, lda, jpvt, tmp, m, st); ++h->launch_count;
@@ -1150,7 +1160,8 @@ static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double
     const size_t need = single_layout(m, n, ctx.params.qr_first && m > n,
                                       ctx.params.precond >= MPJSVD_PRECOND_L,
                                       ctx.params.gemm_kernel == MPJSVD_GEMMK_TC ||
-                                          (ctx.params.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN)).total;
+                                          (ctx.params.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN &&
+                                           n <= kGemmTcMaxN)).total;
     if (state_bytes + need > kNoAllocBytes)
         return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
                          cudaErrorInvalidValue);

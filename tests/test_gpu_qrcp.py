@@ -33,9 +33,12 @@ def _graded(rng, m, n, ratio):
     return rng.standard_normal((m, n)) * (ratio ** -np.arange(n))[rng.permutation(n)]
 
 
-@pytest.mark.parametrize("qrcp", ["mixed", "f64"])
-@pytest.mark.parametrize("m,n", [(60, 30), (300, 200), (2048, 1024)])
+@pytest.mark.parametrize("qrcp,m,n", [(q, m, n) for q in ("mixed", "f64")
+                                      for m, n in [(60, 30), (300, 200), (2048, 1024)]] +
+                         [("mixed", 10300, 610)])
 def test_pivots_exact_on_graded_columns(qrcp, m, n):
+    """(10300, 610): columns too long for the register- and shared-memory-resident binary32
+    search, so Alg. 5 keeps them in global memory."""
     rng = np.random.default_rng(m + n)
     A = _graded(rng, m, n, 10.0 ** (min(30, 200) / n * 0.6 + 0.02)) if n > 30 else _graded(rng, m, n, 10.0)
     QR, jpvt, tau, st = _gpu_geqp3(A, qrcp)
@@ -44,21 +47,26 @@ def test_pivots_exact_on_graded_columns(qrcp, m, n):
     assert np.array_equal(jpvt, jo)
 
 
-@pytest.mark.parametrize("qrcp", ["mixed", "f64"])
-@pytest.mark.parametrize("m,n", [(200, 120), (1000, 333), (2048, 1024)])
+@pytest.mark.parametrize("qrcp,m,n", [(q, m, n) for q in ("mixed", "f64")
+                                      for m, n in [(200, 120), (1000, 333), (2048, 1024)]] +
+                         [("mixed", 10300, 610)])
 def test_rrqr_property_and_r_parity(qrcp, m, n):
     rng = np.random.default_rng(7 * m + n)
     A = inputs.known_sigma(rng, m, n, np.logspace(0, -5, n)) * rng.uniform(0.1, 10.0, n)
     QR, jpvt, tau, st = _gpu_geqp3(A, qrcp)
     assert sorted(jpvt.tolist()) == list(range(n))
     R = np.triu(QR[:n])
-    # every pivot had the largest remaining norm, up to the accuracy of the downdated norms:
-    # they are recomputed only once a downdate has lost about sqrt(u) (2^-12 in binary32,
-    # 2^-26.5 in binary64), so the choice is exact to about 2 sqrt(u)
+    # every pivot had the largest remaining norm, up to the accuracy of the norms the search
+    # compares: the downdated norms are recomputed only once a downdate has lost about sqrt(u)
+    # (2^-12 in binary32, 2^-26.5 in binary64), so the choice is exact to about 2 sqrt(u)
+    # relative; and the remaining columns themselves carry the search precision's rounding of
+    # m-term dot products, about m u |a_k| absolute (binary32: what Alg. 5 trades for speed)
     slack = 2 * 2.0 ** -12 if qrcp == "mixed" else 2 * 2.0 ** -26.5
+    u_s = 2.0 ** -24 if qrcp == "mixed" else 2.0 ** -53
+    absl = m * u_s * np.linalg.norm(A, axis=0).max()
     rem = np.sqrt(np.cumsum((R ** 2)[::-1], axis=0)[::-1])  # rem[j, k] = |R(j:, k)|
     for j in range(n):
-        assert abs(R[j, j]) >= (1 - slack) * rem[j, j:].max()
+        assert abs(R[j, j]) >= (1 - slack) * rem[j, j:].max() - absl, j
     # R and the reflectors equal the oracle's binary64 QR of A P for the GPU's P
     QRo, tauo = oracle.geqrf(A[:, jpvt])
     scale = np.abs(A).max() * np.sqrt(m)
