@@ -92,6 +92,13 @@ extern "C" {
                                 mpjsvd_dgemm_tc) */
 #define MPJSVD_GEMMK_F64 2   /* the FP64 pipe (register-blocked SIMT kernel) */
 
+/* params.work_kernel: the visits of the binary64 sweeps (Section 3.4, Alg. 1). */
+#define MPJSVD_WORKK_AUTO 0    /* cluster-split visits when a block pair of width 4 does not fit
+                                  one CTA's registers (more than 2048 rows), else one CTA per visit */
+#define MPJSVD_WORKK_CLUSTER 1 /* every visit split by rows over a thread-block cluster of 2, 4 or
+                                  8 CTAs (block width 4; up to 16384 rows) */
+#define MPJSVD_WORKK_CTA 2     /* one CTA per visit, the block pair in its registers */
+
 /* params.switch_method: the precision switch of Section 3.3. */
 #define MPJSVD_SWITCH_U 0    /* B = X^T U_low, B = Q R2, Y = X Q (the method the paper prefers;
                                 default) */
@@ -139,6 +146,9 @@ typedef struct {
                              threshold (Y2 = the columns of Y from the first one whose largest
                              cosine with an earlier column exceeds y_tol: Alg. 1 on Y2, one pass
                              over the Y1 x Y2 pairs, then the refinement); 0 (default): off */
+    int work_kernel;      /* MPJSVD_WORKK_* */
+    int work_cluster;     /* CTAs per visit of the cluster form: 0 (default) the fewest that hold
+                             the rows (2048 per CTA), or 2, 4, 8 (at least that many) */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */
@@ -171,6 +181,7 @@ typedef struct {
     int n_flagged;        /* near-degenerate count of the handle's last mpjsvd_svd_backward
                              (pairs with |s_i - s_j| <= gap_tol max(s_i, s_j) plus s_i <= 2^-53 s_0);
                              -1 if the handle has run none */
+    int work_cluster;     /* CTAs per visit of the binary64 sweeps (1: one CTA per visit) */
 } mpjsvd_stats;
 
 /* Fill *p with the defaults. Returns 0, or -1 if p is NULL. */

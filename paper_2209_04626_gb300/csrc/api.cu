@@ -91,6 +91,8 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->switch_method = MPJSVD_SWITCH_U;
     p->gemm_kernel = MPJSVD_GEMMK_AUTO;
     p->y_tol = 0.0;
+    p->work_kernel = MPJSVD_WORKK_AUTO;
+    p->work_cluster = 0;
     return 0;
 }
 
@@ -109,6 +111,8 @@ static int check_params(const mpjsvd_params* p)
     if (p->switch_method < 0 || p->switch_method > 1) return 1;
     if (p->gemm_kernel < 0 || p->gemm_kernel > 2) return 1;
     if (!(p->y_tol >= 0.0 && p->y_tol < 1.0)) return 1;
+    if (p->work_kernel < 0 || p->work_kernel > 2) return 1;
+    if (p->work_cluster != 0 && p->work_cluster != 2 && p->work_cluster != 4 && p->work_cluster != 8) return 1;
     return 0;
 }
 

@@ -32,6 +32,13 @@
 #include "sweep.cuh"
 #include "tc.cuh"
 
+// Phase probes of a visit: empty here; a profiling build may define them to record per-phase
+// times (PROBE_BEGIN declares its state, PROBE(i) closes phase i).
+#ifndef MPJ_TC_PROBE_BEGIN
+#define MPJ_TC_PROBE_BEGIN
+#define MPJ_TC_PROBE(i)
+#endif
+
 namespace mpj {
 
 constexpr int kBW = 64;         // block width
@@ -97,61 +104,97 @@ __device__ __forceinline__ bool drain(BVisitShared& s, int i, DevState* st)
     return true;
 }
 
-// Loads of the Gram step for one chunk of kGramKC = 32 rows: 16 groups of 8 columns, two per
-// warp; lane: column 8 cg + (lane & 7), rows 8 (lane >> 3) .. + 7 of the chunk.
-__device__ __forceinline__ void gram_load(const float* X, int ldX, int mX, const BVisitShared& s, int ch,
-                                          float (&v)[2][8])
+// Pieces of the Gram step's chunks of 32 rows (16 bytes each): the chunk is
+// 128 columns x 8 pieces (rows 4 k4 .. 4 k4 + 3); warp w takes units w, w + 8, w + 16, w + 24,
+// unit = (group of 8 columns cg, half kh of the chunk's rows); lane: column 8 cg + (lane & 7),
+// piece k4 = 4 kh + (lane >> 3). A warp's load covers 8 columns x 64 contiguous bytes (whole
+// 32-byte sectors), and the piece is one row of a K-major core matrix of the MMA operand.
+__device__ __forceinline__ void gram_piece(int unit, int lane, int& cg, int& c, int& k4)
+{
+    cg = unit >> 1;
+    c = cg * 8 + (lane & 7);
+    k4 = (unit & 1) * 4 + (lane >> 3);
+}
+
+// Raw staging of the Gram step: kGramStages chunks in flight (cp.async, this thread's four
+// pieces of a chunk at ((u * 8 + warp) * 32 + lane) * 16 of its stage), in the G and W regions,
+// which hold nothing until the Gram is read back.
+constexpr int kGramStages = 8;
+constexpr size_t kGramRaw = 16384;  // one chunk: 128 columns x 32 rows of binary32
+static_assert(kGramStages * kGramRaw <= kRegG + kRegW, "raw Gram stages must fit the G and W regions");
+
+// Issue the copies of chunk ch into a raw stage. Rows at or beyond mX and phantom columns are
+// zero-filled (their source address stays at the column's start). vec: X and ldX allow aligned
+// 16-byte copies (else four 4-byte copies per piece).
+__device__ __forceinline__ void gram_issue(const float* X, int ldX, int mX, const BVisitShared& s, int ch,
+                                           bool vec, unsigned char* raw)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int rep = 0; rep < 2; ++rep) {
-        const int c = (warp + 8 * rep) * 8 + (lane & 7);
+    for (int u = 0; u < 4; ++u) {
+        int cg, c, k4;
+        gram_piece(warp + 8 * u, lane, cg, c, k4);
         const int gc = s.gidx[c];
-        const int row0 = ch * 32 + 8 * (lane >> 3);
-        const float* col = X + (size_t)(gc < 0 ? 0 : gc) * ldX;
+        const int r = ch * 32 + 4 * k4;
+        const float* base = X + (size_t)(gc < 0 ? 0 : gc) * ldX;
+        const int nv = (gc < 0) ? 0 : max(0, min(4, mX - r));  // rows of the piece inside X
+        unsigned char* d = raw + (size_t)((u * 8 + warp) * 32 + lane) * 16;
+        if (vec) {
+            cp_async16(d, nv > 0 ? base + r : base, 4 * nv);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = row0 + i;
-            v[rep][i] = (gc >= 0 && r < mX) ? __ldcg(col + r) : 0.0f;
+            for (int e = 0; e < 4; ++e) cp_async4(d + 4 * e, e < nv ? base + r + e : base, e < nv ? 4 : 0);
         }
     }
 }
 
 // 1. G = Z^T Z into shared memory (row stride kGP); Z = columns gidx[] of X, rows 0..mX-1.
-// The loads of chunk ch + 1 are issued while the MMAs of chunk ch run. Returns false if a
-// wait gave up.
+// Chunks of 32 rows stream in by cp.async, kGramStages - 1 ahead of the one being split; the
+// MMAs of a chunk run while the next is split. Returns false if a wait gave up.
 __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsigned char* dsm,
                           float* G, DevState* st)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nch = (mX + 31) / 32;
-    float v[2][8];
-    gram_load(X, ldX, mX, s, 0, v);
+    const bool vec = (ldX % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+    unsigned char* rawb = dsm + kRegStage;
+#pragma unroll 1
+    for (int c = 0; c < kGramStages - 1; ++c) {
+        if (c < nch) gram_issue(X, ldX, mX, s, c, vec, rawb + (size_t)c * kGramRaw);
+        cp_async_commit();
+    }
     for (int ch = 0; ch < nch; ++ch) {
+        const int nx = ch + kGramStages - 1;
+        if (nx < nch) gram_issue(X, ldX, mX, s, nx, vec, rawb + (size_t)(nx % kGramStages) * kGramRaw);
+        cp_async_commit();
         const int buf = ch & 1;
-        if (!drain(s, buf, st)) return false;  // MMAs of chunk ch - 2 have read the buffer
+        if (!drain(s, buf, st)) {  // MMAs of chunk ch - 2 have read the buffer
+            cp_async_wait_all();
+            return false;
+        }
+        cp_async_wait<kGramStages - 1>();  // this thread's copies of chunk ch have landed
+        const unsigned char* raw = rawb + (size_t)(ch % kGramStages) * kGramRaw;
         unsigned char* hi = dsm + buf * 32768;
         unsigned char* lo = hi + 16384;
-        // two 16-byte pieces per group: core matrices k4 = 2 (lane >> 3) and + 1 of row group cg
+        // one core-matrix row per piece: row group cg, k group k4, row c & 7
 #pragma unroll
-        for (int rep = 0; rep < 2; ++rep) {
-            const int cg = warp + 8 * rep, c = cg * 8 + (lane & 7), rg = lane >> 3;
+        for (int u = 0; u < 4; ++u) {
+            int cg, c, k4;
+            gram_piece(warp + 8 * u, lane, cg, c, k4);
+            const float4 x4 = *(const float4*)(raw + (size_t)((u * 8 + warp) * 32 + lane) * 16);
+            float4 h4, l4;
+            const float* xp = &x4.x;
+            float* hp = &h4.x;
+            float* lp = &l4.x;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                float4 h4, l4;
-                float* hp = &h4.x;
-                float* lp = &l4.x;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float x = v[rep][4 * q + e];
-                    const float hx = tf32_rna(x);
-                    hp[e] = hx;
-                    lp[e] = tf32_rna(x - hx);
-                }
-                const size_t off = (size_t)cg * 1024 + (size_t)(2 * rg + q) * 128 + (size_t)(c & 7) * 16;
-                *(float4*)(hi + off) = h4;
-                *(float4*)(lo + off) = l4;
+            for (int e = 0; e < 4; ++e) {
+                const float hx = tf32_rna(xp[e]);
+                hp[e] = hx;
+                lp[e] = tf32_rna(xp[e] - hx);
             }
+            const size_t off = (size_t)cg * 1024 + (size_t)k4 * 128 + (size_t)(c & 7) * 16;
+            *(float4*)(hi + off) = h4;
+            *(float4*)(lo + off) = l4;
         }
         fence_async_smem();
         __syncthreads();
@@ -168,8 +211,8 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             tc_commit(&s.mbar[buf]);
             ++s.pend[buf];
         }
-        if (ch + 1 < nch) gram_load(X, ldX, mX, s, ch + 1, v);
     }
+    cp_async_wait_all();  // (only empty groups remain) before G overwrites the raw stages
     if (!drain(s, 0, st) || !drain(s, 1, st)) return false;
     // read back: warp w holds lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
     const int base = 32 * (warp & 3), c0 = 64 * (warp >> 2);
@@ -443,9 +486,12 @@ __device__ int bvisit(const SweepDims& D, float* X, int bi, int bj, bool first, 
     float* G = (float*)(dsm + kRegStage);
     float* W = (float*)(dsm + kRegStage + kRegG);
     if (!gram_tf32(X, D.ldX, D.mX, s, dsm, G, st)) return -1;
+    MPJ_TC_PROBE(1)
     const int nrot = rotate_gram(G, W, first, (float)D.tol, s,
                                  (const unsigned short*)(dsm + kRegStage + kRegG + kRegW));
+    MPJ_TC_PROBE(2)
     if (nrot > 0 && !apply_tf32(X, D.ldX, D.mX, s, dsm, W, st)) return -1;
+    MPJ_TC_PROBE(3)
     return nrot;
 }
 
@@ -463,7 +509,9 @@ __device__ int bsweeps_flow(const Group& g, const SweepDims& D, float* X, unsign
             rr_pair(k, r, i, bi, bj);
             if (bi > bj) { const int t = bi; bi = bj; bj = t; }
             const unsigned R = (unsigned)(sweep * rounds + r);
+            MPJ_TC_PROBE_BEGIN
             if (!wait_blocks(D.ver, bi, bj, R, g.st)) return -1;
+            MPJ_TC_PROBE(0)
             const int nrot = bvisit(D, X, bi, bj, r == 0, s, dsm, g.st);
             if (nrot < 0) return -1;
             __syncthreads();

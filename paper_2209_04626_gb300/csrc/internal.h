@@ -29,6 +29,7 @@ struct mpjsvd_ctx {
     mpjsvd_stats last;
     bool last_valid;
     int last_block_w_low, last_block_w_work;
+    int last_work_cs;  // CTAs per visit of the last call's binary64 sweeps
     int launch_count;  // kernels launched by the last call
     int last_qrcp;     // MPJSVD_QRCP_* that the last call ran
     int last_precond;  // MPJSVD_PRECOND_* of the last call (AUTO resolved from the device)
@@ -79,6 +80,13 @@ int tc_block_call(mpjsvd_ctx* h, int m, float* Z, int ldz, float* G, const float
 // largest block width <= w_want whose register-resident visit holds mX rows (0: none)
 int sweep_fit_w_f32(int mX, int w_want);
 int sweep_fit_w_f64(int mX, int w_want);
+// binary64 sweeps with every visit split by rows over a cluster of cs CTAs (sweep_cl.cu):
+// cs for mX rows under params.work_kernel (0: one CTA per visit), the block width, and the
+// launch (1 = cluster launch unavailable here, nothing launched)
+int sweep_cl_size(int mX, int work_kernel, int min_cs);
+int sweep_cl_width();
+int launch_sweeps_f64_cl(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st, int phase,
+                         int gate_want, int cs);
 
 // blocked Householder QR and compact-WY application of Q (qr_blocked.cu)
 int bqr_nb(int m);                       // panel width for m rows; 0: use the unblocked kernels

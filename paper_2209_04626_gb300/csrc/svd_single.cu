@@ -852,11 +852,31 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     const bool low_tc = !alt_switch && (P.low_kernel == MPJSVD_LOWK_TC ||
                                         (P.low_kernel == MPJSVD_LOWK_AUTO && n >= kLowTcMinN));
     int w_low = low_tc ? 64 : sweep_fit_w_f32(n, pick_w(n, n, true, h->num_sms, P.block_w));
-    int w_work = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
-    if (w_low == 0 || w_work == 0)
+    // binary64 sweeps: one CTA per visit (width limited by its registers for tall Y), or every
+    // visit split by rows over a cluster (block width 4)
+    const int w_cta = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
+    const int work_cs = sweep_cl_size(n, P.work_kernel, P.work_cluster);
+    int w_work = work_cs ? sweep_cl_width() : w_cta;
+    if (w_low == 0 || (w_cta == 0 && work_cs == 0))
         return cuda_fail("sweeps: no register-resident variant holds n rows", cudaErrorInvalidValue);
     h->last_block_w_low = (P.mode == MPJSVD_MODE_PLAIN) ? 0 : w_low;
     h->last_block_w_work = w_work;
+    h->last_work_cs = work_cs ? work_cs : 1;
+    // a binary64 sweep stage on Y (and V): the cluster form, else (or where the cluster launch is
+    // unavailable) the single-CTA form at its own width
+    auto work_sweeps = [&](const SweepDims& D, double* Yp, double* Vp, int phase, int gate) -> int {
+        if (work_cs) {
+            const int r = launch_sweeps_f64_cl(h, D, Yp, Vp, st, phase, gate, work_cs);
+            if (r != 1) return r;
+            if (w_cta == 0) return cuda_fail("sweeps: cluster launch unavailable", cudaErrorNotSupported);
+            h->last_block_w_work = w_cta;
+            h->last_work_cs = 1;
+        }
+        SweepDims Dc = D;
+        Dc.w = w_cta;
+        Dc.k = sweep_blocks(D.n, w_cta);
+        return launch_sweeps_f64(h, Dc, Yp, Vp, st, phase, gate, nullptr);
+    };
     if (P.mode != MPJSVD_MODE_PLAIN) {
         k_to_float<<<egrid, T256, 0, s>>>(nn, X, Xl, st); ++h->launch_count;
         const double tol_low = std::sqrt((double)n) * 5.9604644775390625e-08;
@@ -948,20 +968,20 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         SweepDims Dy = Dw;
         Dy.filter = 1;
         Dy.j0 = &st->y_j0;
-        if ((rc = launch_sweeps_f64(h, Dy, Y, Vacc, st, 2, kGateY2 + 1, nullptr))) return rc;
+        if ((rc = work_sweeps(Dy, Y, Vacc, 2, kGateY2 + 1))) return rc;
         Dy.filter = 2;
         Dy.maxsweep = 1;
-        if ((rc = launch_sweeps_f64(h, Dy, Y, Vacc, st, 2, kGateY2 + 1, nullptr))) return rc;
+        if ((rc = work_sweeps(Dy, Y, Vacc, 2, kGateY2 + 1))) return rc;
     }
     if (!P.v_by_qr) {
-        if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 1, -1, nullptr))) return rc;
+        if ((rc = work_sweeps(Dw, Y, Vacc, 1, -1))) return rc;
     } else {
         // V from the QR of X^T U_X (Section 3.4): Alg. 1 on Y without V; U_X = the normalized
         // columns of Y sorted by descending norm; B3 = X^T U_X = Q3 R3; Y = X Q3 and Alg. 1
         // with V accumulated from V_acc = Q3
         SweepDims Dn = Dw;
         Dn.nV = 0;
-        if ((rc = launch_sweeps_f64(h, Dn, Y, nullptr, st, 1, -1, nullptr))) return rc;
+        if ((rc = work_sweeps(Dn, Y, nullptr, 1, -1))) return rc;
         k_colnorms<<<std::max(1, (n * 32 + T256 - 1) / T256), T256, 0, s>>>(n, n, Y, n, sig); ++h->launch_count;
         k_rank_desc<double><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sig, ord2, st, -1); ++h->launch_count;
         k_make_ux<<<std::min(n, egrid), T256, 0, s>>>(n, Y, sig, ord2, Ul, st); ++h->launch_count;
@@ -982,7 +1002,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g4.klo_from_row = x_upper;
         g4.khi_from_row = x_lower;
         if ((rc = gemm64(g4, nullptr, 0))) return rc;
-        if ((rc = launch_sweeps_f64(h, Dw, Y, Vacc, st, 2, -1, nullptr))) return rc;
+        if ((rc = work_sweeps(Dw, Y, Vacc, 2, -1))) return rc;
     }
     record(h, 5);
 
@@ -1078,6 +1098,7 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     r.orth = st.orth;
     r.block_w_low = st.branch == 0 ? h->last_block_w_low : 0;
     r.block_w_work = h->last_block_w_work;
+    r.work_cluster = h->last_work_cs;
     r.launches = h->launch_count;
     r.qrcp = h->last_qrcp;
     r.precond = h->last_precond >= MPJSVD_PRECOND_L ? (st.gate_lq ? MPJSVD_PRECOND_L : MPJSVD_PRECOND_R)

@@ -24,6 +24,7 @@ STOP = {"xgesvj": 0, "alg1": 1}
 LOWK = {"auto": 0, "tc": 1, "reg": 2}
 SWITCH = {"u": 0, "v": 1}
 GEMMK = {"auto": 0, "tc": 1, "f64": 2}
+WORKK = {"auto": 0, "cluster": 1, "cta": 2}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -42,7 +43,8 @@ class Params(ctypes.Structure):
                 ("precond", ctypes.c_int), ("qr_first", ctypes.c_int), ("timing", ctypes.c_int),
                 ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("low_kernel", ctypes.c_int), ("v_by_qr", ctypes.c_int),
-                ("switch_method", ctypes.c_int), ("gemm_kernel", ctypes.c_int), ("y_tol", ctypes.c_double)]
+                ("switch_method", ctypes.c_int), ("gemm_kernel", ctypes.c_int), ("y_tol", ctypes.c_double),
+                ("work_kernel", ctypes.c_int), ("work_cluster", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +57,7 @@ class Stats(ctypes.Structure):
                 ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
                 ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int),
                 ("precond", ctypes.c_int), ("sweeps_v", ctypes.c_int), ("rot_v", ctypes.c_longlong),
-                ("y2_cols", ctypes.c_int), ("n_flagged", ctypes.c_int)]
+                ("y2_cols", ctypes.c_int), ("n_flagged", ctypes.c_int), ("work_cluster", ctypes.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -131,6 +133,8 @@ def mpjsvd_default_params(**overrides):
             v = SWITCH[v]
         if k == "gemm_kernel" and isinstance(v, str):
             v = GEMMK[v]
+        if k == "work_kernel" and isinstance(v, str):
+            v = WORKK[v]
         setattr(p, k, v)
     return p
 
@@ -289,6 +293,8 @@ class Handle:
                 v = SWITCH[v]
             if k == "gemm_kernel" and isinstance(v, str):
                 v = GEMMK[v]
+            if k == "work_kernel" and isinstance(v, str):
+                v = WORKK[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 

@@ -53,3 +53,16 @@ def sigma_gate(A, S_gpu, S_orc):
     e_o = float(np.max(np.abs(np.asarray(S_orc, dtype=np.longdouble) - Se) / Se))
     assert e_g <= max(1e-12, 2.0 * e_o), (e_g, e_o)
     return e_g, e_o
+
+
+def elementwise_vs_oracle(U, S, V, So, Uo, Vo, sig_tol=1e-12, vec_tol=1e-8):
+    """Element-wise parity with a binary64 oracle SVD of the same stored A: singular values to
+    sig_tol relative, singular vectors (after sign alignment) where the singular values are
+    separated by >= 1e-3."""
+    assert np.max(np.abs(S - So) / So) <= sig_tol, np.max(np.abs(S - So) / So)
+    gaps = np.minimum(np.r_[np.inf, -np.diff(So)], np.r_[-np.diff(So), np.inf]) / So
+    sep = gaps >= 1e-3
+    assert sep.sum() > len(So) // 2
+    Ua, Va = align_signs(U, V, Uo, Vo)
+    assert np.abs(Va[:, sep] - Vo[:, sep]).max() <= vec_tol
+    assert np.abs(Ua[:, sep] - Uo[:, sep]).max() <= vec_tol

@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 from paper_2209_04626_gb300 import inputs
-from tests.gpu_util import check_factorization, check_sign_rule, gpu_svd, sigma_gate
+from tests.gpu_util import (check_factorization, check_sign_rule, elementwise_vs_oracle, gpu_svd,
+                            sigma_gate)
 
 pytestmark = pytest.mark.gpu
 
@@ -36,16 +37,7 @@ def test_precision_2048x1024_full():
 
 
 def _vs_oracle(A, U, S, V, So, Uo, Vo, sig_tol=1e-12, vec_tol=1e-8):
-    """Element-wise parity with the oracle: singular values to sig_tol relative, singular
-    vectors (after sign alignment) where the singular values are separated by >= 1e-3."""
-    from tests.gpu_util import align_signs
-    assert np.max(np.abs(S - So) / So) <= sig_tol, np.max(np.abs(S - So) / So)
-    gaps = np.minimum(np.r_[np.inf, -np.diff(So)], np.r_[-np.diff(So), np.inf]) / So
-    sep = gaps >= 1e-3
-    assert sep.sum() > len(So) // 2
-    Ua, Va = align_signs(U, V, Uo, Vo)
-    assert np.abs(Va[:, sep] - Vo[:, sep]).max() <= vec_tol
-    assert np.abs(Ua[:, sep] - Uo[:, sep]).max() <= vec_tol
+    elementwise_vs_oracle(U, S, V, So, Uo, Vo, sig_tol, vec_tol)
 
 
 def test_precision_2048x1024_vs_oracle():
@@ -62,11 +54,12 @@ def test_precision_2048x1024_vs_oracle():
 
 def test_large_recipe_at_1024_vs_oracle():
     """The large workload's recipe (A = B D, B sigma 1 .. 1e-2, D = diag(10^U(-10, 0))) at
-    n = 1024, mixed and plain, against the binary64 oracle."""
+    n = 1024, mixed and plain, and the binary64 sweeps in both forms (one CTA per visit, visits
+    split over a cluster), against the binary64 oracle."""
     A = inputs.large_8192(n=1024)
     Uo, So, Vo, sto = oracle.svd(A, mode="mixed")
-    for mode in ("mixed", "plain"):
-        U, S, V, st = gpu_svd(A, mode)
+    for mode, wk in (("mixed", "auto"), ("plain", "auto"), ("mixed", "cta"), ("mixed", "cluster")):
+        U, S, V, st = gpu_svd(A, mode, work_kernel=wk)
         assert st["status"] == 0, st
         check_factorization(A, U, S, V)
         check_sign_rule(V)

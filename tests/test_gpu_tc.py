@@ -37,7 +37,7 @@ def _block(Z, W=None, gram=True):
     return Gh, out
 
 
-@pytest.mark.parametrize("m", [1, 31, 128, 300, 1024, 4099])
+@pytest.mark.parametrize("m", [1, 31, 128, 300, 1024, 4099, 4100, 8202])
 def test_tc_gram_tf32x3(m):
     """G = Z^T Z: within the binary32 error bound of a dot product, 2 m u_32 |z_i| |z_j| (the
     3-term split drops only lo lo', about 2^-22 of each product), against the binary64
