@@ -172,6 +172,7 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             cp_async_wait_all();
             return false;
         }
+        MPJ_TC_PROBE(4)
         cp_async_wait<kGramStages - 1>();  // this thread's copies of chunk ch have landed
         const unsigned char* raw = rawb + (size_t)(ch % kGramStages) * kGramRaw;
         unsigned char* hi = dsm + buf * 32768;
@@ -198,6 +199,7 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
         }
         fence_async_smem();
         __syncthreads();
+        MPJ_TC_PROBE(5)
         if (tid == 0) {
             tc_fence_after();
 #pragma unroll
@@ -211,6 +213,7 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             tc_commit(&s.mbar[buf]);
             ++s.pend[buf];
         }
+        MPJ_TC_PROBE(6)
     }
     cp_async_wait_all();  // (only empty groups remain) before G overwrites the raw stages
     if (!drain(s, 0, st) || !drain(s, 1, st)) return false;

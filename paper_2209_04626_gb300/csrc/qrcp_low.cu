@@ -20,7 +20,9 @@
 namespace mpj {
 
 constexpr int kLowThreads = 256;
+constexpr int kLowThreadsGlobal = 512;  // columns in global memory: more loads in flight
 constexpr int kLowBatch = 4;
+constexpr int kLowUnroll = 4;  // rows per thread whose loads are issued together
 
 __device__ __forceinline__ float block_max_f(float v, float* red)
 {
@@ -63,7 +65,7 @@ __host__ __device__ inline size_t qrcp_low_smem_bytes(int m, int n, int gsize, b
 // GLOBAL = false: the owned columns in shared memory; GLOBAL = true (columns too long for it):
 // in global memory, gcols + rank * own_max * m (L2 and HBM traffic instead of shared memory).
 template <bool GLOBAL>
-__global__ void __launch_bounds__(kLowThreads)
+__global__ void __launch_bounds__(GLOBAL ? kLowThreadsGlobal : kLowThreads)
     k_qrcp_low(int m, int n, const double* __restrict__ A, int lda, int* perm, float* bcast,
                DevState* st, float* gcols)
 {
@@ -194,7 +196,25 @@ __global__ void __launch_bounds__(kLowThreads)
                 float acc[kLowBatch], w[kLowBatch];
 #pragma unroll
                 for (int b = 0; b < kLowBatch; ++b) acc[b] = 0.0f;
-                for (int i = j + 1 + tid; i < m; i += nthr) {
+                // kLowUnroll rows at a time: their loads are in flight together; each thread
+                // still sums its rows in increasing order
+                int i = j + 1 + tid;
+                if (GLOBAL) {
+                    for (; i + (kLowUnroll - 1) * nthr < m; i += kLowUnroll * nthr) {
+                        float vu[kLowUnroll], cu[kLowUnroll][kLowBatch];
+#pragma unroll
+                        for (int u = 0; u < kLowUnroll; ++u) {
+                            vu[u] = vs[i + u * nthr];
+#pragma unroll
+                            for (int b = 0; b < kLowBatch; ++b) cu[u][b] = cols[b][i + u * nthr];
+                        }
+#pragma unroll
+                        for (int u = 0; u < kLowUnroll; ++u)
+#pragma unroll
+                            for (int b = 0; b < kLowBatch; ++b) acc[b] = fmaf(vu[u], cu[u][b], acc[b]);
+                    }
+                }
+                for (; i < m; i += nthr) {
                     const float vi = vs[i];
 #pragma unroll
                     for (int b = 0; b < kLowBatch; ++b) acc[b] = fmaf(vi, cols[b][i], acc[b]);
@@ -205,7 +225,24 @@ __global__ void __launch_bounds__(kLowThreads)
                 __syncthreads();  // every thread has read c_j before it changes
                 if (tid == 0)
                     for (int b = 0; b < nb; ++b) cols[b][j] -= w[b];
-                for (int i = j + 1 + tid; i < m; i += nthr) {
+                i = j + 1 + tid;
+                if (GLOBAL) {
+                    for (; i + (kLowUnroll - 1) * nthr < m; i += kLowUnroll * nthr) {
+                        float vu[kLowUnroll], cu[kLowUnroll][kLowBatch];
+#pragma unroll
+                        for (int u = 0; u < kLowUnroll; ++u) {
+                            vu[u] = vs[i + u * nthr];
+#pragma unroll
+                            for (int b = 0; b < kLowBatch; ++b) cu[u][b] = cols[b][i + u * nthr];
+                        }
+#pragma unroll
+                        for (int u = 0; u < kLowUnroll; ++u)
+#pragma unroll
+                            for (int b = 0; b < kLowBatch; ++b)
+                                if (b < nb) cols[b][i + u * nthr] = fmaf(-w[b], vu[u], cu[u][b]);
+                    }
+                }
+                for (; i < m; i += nthr) {
                     const float vi = vs[i];
 #pragma unroll
                     for (int b = 0; b < kLowBatch; ++b)
@@ -684,12 +721,13 @@ int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* 
     void* kern = global_cols ? (void*)k_qrcp_low<true> : (void*)k_qrcp_low<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail("qrcp_low smem attribute", e);
+    const int threads = global_cols ? kLowThreadsGlobal : kLowThreads;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLowThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return cuda_fail("qrcp_low occupancy", e);
     if (occ < 1) return 1;
     void* args[] = {&m, &n, &A, &lda, &perm, &bcast, &st, &gcols};
-    e = cudaLaunchCooperativeKernel(kern, grid, kLowThreads, args, smem, h->stream);
+    e = cudaLaunchCooperativeKernel(kern, grid, threads, args, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail("qrcp_low launch", e);
     ++h->launch_count;
     return 0;

@@ -77,14 +77,15 @@ def test_cluster_large_recipe_against_oracle(cs):
 @pytest.mark.parametrize("cs", [0, 4, 8])
 def test_cluster_against_single_cta_visits(cs):
     """2304 x 2304 (large recipe): more rows than one CTA's registers hold at block width 4, so
-    the automatic choice takes 2-CTA clusters; 2, 4 and 8 CTAs per visit against single-CTA
-    visits (block width 2): the same singular values to 1e-12, the bars on both."""
+    the automatic choice takes clusters (4 CTAs: at most 1024 rows each); 4 and 8 CTAs per
+    visit against single-CTA visits (block width 2): the same singular values to 1e-12, the
+    bars on both."""
     A = inputs.large_8192(n=2304)
     U0, S0, V0, st0 = gpu_svd(A, mode="mixed", work_kernel="cta")
     assert st0["status"] == 0 and st0["work_cluster"] == 1
     U1, S1, V1, st1 = gpu_svd(A, mode="mixed", work_kernel="auto" if cs == 0 else "cluster", work_cluster=cs)
     assert st1["status"] == 0
-    assert st1["work_cluster"] == (2 if cs == 0 else cs) and st1["block_w_work"] == 4, st1
+    assert st1["work_cluster"] == (4 if cs == 0 else cs) and st1["block_w_work"] == 4, st1
     check_factorization(A, U1, S1, V1)
     assert np.max(np.abs(S1 - S0) / S0) <= 1e-12
     assert st1["sweeps_work"] <= st0["sweeps_work"] + 1
