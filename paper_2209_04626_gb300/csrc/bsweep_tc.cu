@@ -69,6 +69,7 @@ struct BVisitShared {
     int nrot;
     unsigned mxc, mxt;        // binary32 bits: largest cosine and |tan| rotated in the visit
     uint64_t mbar[2];
+    int fail;                 // set by thread 0 when its bounded wait gave up
     uint32_t tmem;
     unsigned pend[2], par[2]; // per mbarrier: commits not yet waited for, parity of the next wait
 };
@@ -87,21 +88,26 @@ __device__ __forceinline__ void bpair(bool intra, int q, int p, int& a, int& b)
     b += base;
 }
 
-// Wait (bounded) for every commit issued on mbarrier i that has not been waited for. Starts
-// with a CTA barrier, so every thread sees the count that thread 0 (the MMA issuer) left.
-__device__ __forceinline__ bool drain(BVisitShared& s, int i, DevState* st)
+// Thread 0 (the MMA issuer) waits (bounded) for every commit on mbarrier i that has not been
+// waited for; then one CTA barrier. False for every thread if the wait gave up.
+__device__ __forceinline__ bool drain1(BVisitShared& s, int i, DevState* st)
 {
-    __syncthreads();
-    while (s.pend[i]) {
-        if (!mbar_wait(&s.mbar[i], s.par[i], st)) return false;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        while (s.pend[i]) {
+            if (!mbar_wait1(&s.mbar[i], s.par[i], st)) {
+                ok = 0;
+                break;
+            }
             s.par[i] ^= 1u;
             --s.pend[i];
         }
-        __syncthreads();
+        s.fail = !ok;
     }
-    return true;
+    __syncthreads();
+    const bool ok = !s.fail;
+    if (ok) tc_fence_after();
+    return ok;
 }
 
 // Pieces of the Gram step's chunks of 32 rows (16 bytes each): the chunk is
@@ -168,12 +174,12 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
         if (nx < nch) gram_issue(X, ldX, mX, s, nx, vec, rawb + (size_t)(nx % kGramStages) * kGramRaw);
         cp_async_commit();
         const int buf = ch & 1;
-        if (!drain(s, buf, st)) {  // MMAs of chunk ch - 2 have read the buffer
+        cp_async_wait<kGramStages - 1>();  // this thread's copies of chunk ch have landed
+        if (!drain1(s, buf, st)) {  // MMAs of chunk ch - 2 have read the buffer
             cp_async_wait_all();
             return false;
         }
         MPJ_TC_PROBE(4)
-        cp_async_wait<kGramStages - 1>();  // this thread's copies of chunk ch have landed
         const unsigned char* raw = rawb + (size_t)(ch % kGramStages) * kGramRaw;
         unsigned char* hi = dsm + buf * 32768;
         unsigned char* lo = hi + 16384;
@@ -216,7 +222,7 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
         MPJ_TC_PROBE(6)
     }
     cp_async_wait_all();  // (only empty groups remain) before G overwrites the raw stages
-    if (!drain(s, 0, st) || !drain(s, 1, st)) return false;
+    if (!drain1(s, 0, st) || !drain1(s, 1, st)) return false;
     // read back: warp w holds lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
     const int base = 32 * (warp & 3), c0 = 64 * (warp >> 2);
     const int row = base + lane;
@@ -329,7 +335,7 @@ __device__ bool apply_tf32(float* X, int ldX, int mX, BVisitShared& s, unsigned 
         const int r0 = ch * 128;
         const uint32_t acc = s.tmem + 128u * (uint32_t)(ch & 1);
         for (int hlf = 0; hlf < 2; ++hlf) {
-            if (!drain(s, 0, st)) return false;  // every MMA issued so far is complete
+            if (!drain1(s, 0, st)) return false;  // every MMA issued so far is complete
             apply_store_a(ahi, alo, v);
             fence_async_smem();
             __syncthreads();
@@ -359,7 +365,7 @@ __device__ bool apply_tf32(float* X, int ldX, int mX, BVisitShared& s, unsigned 
             }
         }
     }
-    if (!drain(s, 0, st)) return false;
+    if (!drain1(s, 0, st)) return false;
     apply_epilogue(X, ldX, mX, s, (nch - 1) * 128, s.tmem + 128u * (uint32_t)((nch - 1) & 1));
     tc_fence_before();
     __syncthreads();

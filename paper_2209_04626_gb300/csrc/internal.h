@@ -83,8 +83,8 @@ int sweep_fit_w_f64(int mX, int w_want);
 // binary64 sweeps with every visit split by rows over a cluster of cs CTAs (sweep_cl.cu):
 // cs for mX rows under params.work_kernel (0: one CTA per visit), the block width, and the
 // launch (1 = cluster launch unavailable here, nothing launched)
-int sweep_cl_size(int mX, int work_kernel, int min_cs);
-int sweep_cl_width();
+int sweep_cl_width(int block_w);
+int sweep_cl_size(int mX, int work_kernel, int min_cs, int w);
 int launch_sweeps_f64_cl(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V, DevState* st, int phase,
                          int gate_want, int cs);
 

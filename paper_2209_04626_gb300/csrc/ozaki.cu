@@ -165,22 +165,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait1(uint64_t* mbar, uint32_t parity, DevState* st)
-{
-    const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
-    unsigned spins = 0;
-    while (!mbar_test(mbar, parity)) {
-        if ((++spins & 1023u) == 0) {
-            if (call_failed(st)) return false;
-            if (globaltimer_ns() - t0 > lim) {
-                atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
-                return false;
-            }
-        }
-    }
-    return true;
-}
-
 struct OzArgs {
     int M, N, K, KB;             // KB = padded k / kOzTK
     const unsigned char* Asl;    // split A: [mb][kb][slice] blocks of kOzABlk

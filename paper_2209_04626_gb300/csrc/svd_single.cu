@@ -855,8 +855,9 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // binary64 sweeps: one CTA per visit (width limited by its registers for tall Y), or every
     // visit split by rows over a cluster (block width 4)
     const int w_cta = sweep_fit_w_f64(n, pick_w(n, n, false, h->num_sms, P.block_w));
-    const int work_cs = sweep_cl_size(n, P.work_kernel, P.work_cluster);
-    int w_work = work_cs ? sweep_cl_width() : w_cta;
+    const int w_cl = sweep_cl_width(P.block_w);
+    const int work_cs = sweep_cl_size(n, P.work_kernel, P.work_cluster, w_cl);
+    int w_work = work_cs ? w_cl : w_cta;
     if (w_low == 0 || (w_cta == 0 && work_cs == 0))
         return cuda_fail("sweeps: no register-resident variant holds n rows", cudaErrorInvalidValue);
     h->last_block_w_low = (P.mode == MPJSVD_MODE_PLAIN) ? 0 : w_low;

@@ -165,6 +165,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, DevSt
     return ok != 0;
 }
 
+// One thread waits (bounded) for the phase with this parity; false if it gave up (a wait that
+// ran out of time records MPJSVD_STATUS_TIMEOUT) or the call failed elsewhere.
+__device__ __forceinline__ bool mbar_wait1(uint64_t* mbar, uint32_t parity, DevState* st)
+{
+    const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
+    unsigned spins = 0;
+    while (!mbar_test(mbar, parity)) {
+        if ((++spins & 1023u) == 0) {
+            if (call_failed(st)) return false;
+            if (globaltimer_ns() - t0 > lim) {
+                atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
 // TF32 rounding (round to nearest, ties away) of a binary32 value: hi part of the 3-term split
 __device__ __forceinline__ float tf32_rna(float x)
 {

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _vs_oracle(A, mode, cs, **opts):
     U, S, V, st = gpu_svd(A, mode=mode, work_kernel="cluster", work_cluster=cs, **opts)
     assert st["status"] in (0, 8), st
-    assert st["work_cluster"] >= cs and st["block_w_work"] == 4, st
+    assert st["work_cluster"] >= cs and st["block_w_work"] == opts.get("block_w", 4), st
     oopts = {k: v for k, v in opts.items() if k in ("y_tol", "v_by_qr")}
     Uo, So, Vo, sto = oracle.svd(A, mode=mode, **oopts)
     check_factorization(A, U, S, V)
@@ -36,6 +36,19 @@ def test_cluster_sweeps_against_oracle(mode, cs):
     A, _ = inputs.plain_256x128()
     st, sto = _vs_oracle(A, mode, cs)
     assert st["sweeps_work"] <= sto["sweeps_work"] + 1
+
+
+@pytest.mark.parametrize("w", [2, 8])
+def test_cluster_block_widths(w):
+    """Block widths 2 and 8 of the cluster form (16 and 4 rows per thread) against the oracle,
+    on the 256 x 128 workload and on a ragged 200-column matrix."""
+    A, _ = inputs.plain_256x128()
+    st, _ = _vs_oracle(A, "mixed", 4, block_w=w)
+    assert st["block_w_work"] == w
+    rng = np.random.default_rng(320 + w)
+    B = inputs.known_sigma(rng, 230, 200, np.logspace(0, -4, 200))
+    st, _ = _vs_oracle(B, "mixed", 2, block_w=w)
+    assert st["block_w_work"] == w
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 7, 33, 130])
