@@ -316,6 +316,16 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 FMA/clk x 2 flop 
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 flop x max clock
 
 
+def _measured_bf16_tflops():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1900.0  # the recipe's fallback burst figure
+
+
+TF32_PEAK_TFLOPS = _measured_bf16_tflops() * 1.1 / 2.25
+
+
 def time_calls(fn, steps, stream, flush):
     import torch
     out = []
@@ -330,25 +340,40 @@ def time_calls(fn, steps, stream, flush):
     return out
 
 
-def traffic_record(m, n):
+def traffic_record(m, n, work_cluster=1):
     """DRAM bytes per launch of the refinement sweeps from a committed ncu summary, used only
-    while the kernel's sources are the ones that were captured (sha256 recorded with it)."""
+    while the kernel's sources are the ones that were captured (sha256 recorded with each
+    record) and for the same form of the kernel (CTAs per visit)."""
     tfile = os.path.join(ROOT, "profiles", "sweep_fp64_traffic.json")
     if not os.path.exists(tfile):
         return None, None
     try:
         tj = json.load(open(tfile))
-        hh = hashlib.sha256()
-        for f in tj.get("sources", []):
-            hh.update(open(os.path.join(ROOT, f), "rb").read())
-        if hh.hexdigest() != tj.get("sources_sha256"):
-            return None, "sources changed since the capture"
-        for rec in tj.get("workloads", []):
-            if rec.get("m") == m and rec.get("n") == n:
-                return rec.get("bytes_per_launch"), rec.get("how")
+        why = "no capture for this size and kernel form"
+        for rec in tj.get("records", []):
+            if rec.get("m") != m or rec.get("n") != n or rec.get("work_cluster", 1) != work_cluster:
+                continue
+            hh = hashlib.sha256()
+            for f in rec.get("sources", []):
+                hh.update(open(os.path.join(ROOT, f), "rb").read())
+            if hh.hexdigest() != rec.get("sources_sha256"):
+                why = "sources changed since the capture"
+                continue
+            return rec.get("bytes_per_launch"), rec.get("how")
     except Exception as ex:  # reported, not fatal
         return None, "unreadable: %s" % ex
-    return None, "no capture for this size"
+    return None, why
+
+
+def tensor_flops_low(m, n, sweeps):
+    """Tensor-core flops of the blocked binary32 stage (64-column blocks, visits of 128 columns):
+    per visit the Gram Z^T Z and the application Z W, each as three TF32 products (the split),
+    2 m 128^2 flops each; every visit counted as rotating (an upper bound: a visit without
+    rotations skips the application)."""
+    k = (n + 63) // 64
+    k += k & 1
+    visits = sweeps * (k - 1) * (k // 2)
+    return visits * 2 * 3 * 2.0 * m * 128 * 128
 
 
 def ours(args):
@@ -417,7 +442,8 @@ def ours(args):
                              for s in per_step_stats)
     phases = {k: statistics.mean(s[k] for s in per_step_stats)
               for k in ["ms_qr", "ms_branch", "ms_low", "ms_switch", "ms_work", "ms_final"]}
-    traffic, traffic_how = traffic_record(m, n)
+    wcl = st["work_cluster"]
+    traffic, traffic_how = traffic_record(m, n, wcl)
 
     # accuracy of the timed outputs (torch FP64 matmuls, verification only)
     with torch.no_grad():
@@ -539,8 +565,14 @@ def ours(args):
                        "parallelism": "replicas",
                        "l2": "flushed (256 MiB write) before each step; inputs %d MiB" % (m * n * 8 >> 20),
                        "block_w_low": st["block_w_low"], "block_w_work": st["block_w_work"],
+                       "work_cluster": wcl,
                        "qrcp": "mixed (Alg. 5)" if st["qrcp"] == 0 else "binary64"},
-            "roofline": {"kernel": "k_sweeps<double> (binary64 refinement sweeps)", "bound": "alu",
+            "roofline": {"kernel": ("k_sweeps_cl<double> (binary64 refinement sweeps, every visit split by "
+                                    "rows over a %d-CTA cluster, block width %d)" % (wcl, st["block_w_work"])
+                                    if wcl > 1 else
+                                    "k_sweeps<double> (binary64 refinement sweeps, one CTA per visit, block "
+                                    "width %d)" % st["block_w_work"]),
+                         "bound": "alu",
                          "achieved": achieved, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_DERIVED, "traffic": traffic,
                          "traffic_source": traffic_how,
@@ -551,7 +583,8 @@ def ours(args):
                                                   "region: independent FP64 FMA chains on every SM"),
                          "flops_per_launch": fl_work, "ms_per_launch": avg_work_ms,
                          "flop_model": "2n per pair per sweep + 12n per rotation (6n on Y, 6n on V)"},
-            "roofline_low": {"kernel": "k_sweeps<float> (binary32 stage)", "bound": "alu",
+            "roofline_low": {"kernel": ("k_bsweeps_tf32 (binary32 stage, tensor cores)" if st["block_w_low"] == 64
+                                        else "k_sweeps<float> (binary32 stage)"), "bound": "alu",
                              "achieved": fl_low / (avg_low_ms / 1000.0) / 1e12 if avg_low_ms > 0 else None,
                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
@@ -577,6 +610,14 @@ def ours(args):
         }
         line["roofline_low"]["frac"] = (line["roofline_low"]["achieved"] / FP32_PEAK_TFLOPS
                                         if line["roofline_low"]["achieved"] else None)
+        if st["block_w_low"] == 64 and avg_low_ms > 0:
+            tfl = tensor_flops_low(n, n, st["sweeps_low"])
+            line["roofline_low"]["tensor"] = {
+                "achieved_upper": tfl / (avg_low_ms / 1000.0) / 1e12, "peak": TF32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac_upper": tfl / (avg_low_ms / 1000.0) / 1e12 / TF32_PEAK_TFLOPS,
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x 1.1 / 2.25 (nominal tf32 : bf16)",
+                "flop_model": "per visit 2 x 3 x 2 m 128^2 (Gram and application, three TF32 products "
+                              "each), every visit counted as rotating"}
         print(json.dumps(line))
     h.close()
     if world > 1:
