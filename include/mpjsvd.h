@@ -99,6 +99,18 @@ extern "C" {
                                   8 CTAs (block width 4; up to 16384 rows) */
 #define MPJSVD_WORKK_CTA 2     /* one CTA per visit, the block pair in its registers */
 
+/* params.qr_update: the trailing updates of the blocked Householder QRs and the applications of
+ * their Q (the preconditioning of Section 3.1, the QR of B and its Q in Section 3.3, U of Alg. 4). */
+#define MPJSVD_QRU_AUTO 0  /* tensor cores for the preconditioner's QR from n = 6144 and for
+                              U = Q [U_R; 0] (and mpjsvd_geqrf / mpjsvd_apply_q) from n = 4096
+                              on; the switch's QR of B and its Q stay on the FP64 pipe (B is
+                              graded by rows, which the split products' per-column scaling does
+                              not follow: the refinement then rotates more) */
+#define MPJSVD_QRU_TC 1    /* two-level everywhere (n > 256): 256-column outer blocks applied in
+                              the compact UT form with the binary64 products on the bf16 tensor
+                              cores (error-free operand splitting, see mpjsvd_dgemm_tc) */
+#define MPJSVD_QRU_F64 2   /* one-level compact-WY updates on the FP64 pipe */
+
 /* params.switch_method: the precision switch of Section 3.3. */
 #define MPJSVD_SWITCH_U 0    /* B = X^T U_low, B = Q R2, Y = X Q (the method the paper prefers;
                                 default) */
@@ -149,6 +161,7 @@ typedef struct {
     int work_kernel;      /* MPJSVD_WORKK_* */
     int work_cluster;     /* CTAs per visit of the cluster form: 0 (default) the fewest that hold
                              the rows (2048 per CTA), or 2, 4, 8 (at least that many) */
+    int qr_update;        /* MPJSVD_QRU_* */
 } mpjsvd_params;
 
 /* Per-call record of what ran (read after the call with mpjsvd_get_stats). */

@@ -93,6 +93,7 @@ int mpjsvd_default_params(mpjsvd_params* p)
     p->y_tol = 0.0;
     p->work_kernel = MPJSVD_WORKK_AUTO;
     p->work_cluster = 0;
+    p->qr_update = MPJSVD_QRU_AUTO;
     return 0;
 }
 
@@ -113,6 +114,7 @@ static int check_params(const mpjsvd_params* p)
     if (!(p->y_tol >= 0.0 && p->y_tol < 1.0)) return 1;
     if (p->work_kernel < 0 || p->work_kernel > 2) return 1;
     if (p->work_cluster != 0 && p->work_cluster != 2 && p->work_cluster != 4 && p->work_cluster != 8) return 1;
+    if (p->qr_update < 0 || p->qr_update > 2) return 1;
     return 0;
 }
 

@@ -25,6 +25,7 @@ struct GemmArgs {
     int ldc;
     bool klo_from_row; // op(A)(i, k) = 0 for k < i
     bool khi_from_row; // op(A)(i, k) = 0 for k > i
+    bool sub = false;  // C <- C - op(A) B (the tensor-core product only)
 };
 
 // One 64 x 64 tile of C, 256 threads, 4 x 4 outputs per thread.

@@ -90,11 +90,29 @@ int launch_sweeps_f64_cl(mpjsvd_ctx* h, const SweepDims& D, double* X, double* V
 
 // blocked Householder QR and compact-WY application of Q (qr_blocked.cu)
 int bqr_nb(int m);                       // panel width for m rows; 0: use the unblocked kernels
-size_t bqr_wbuf_doubles(int ncols_max, int m_max);  // scratch for bqr_factor / bqr_apply
+size_t bqr_wbuf_doubles(int ncols_max, int m_max);  // scratch of the one-level bqr_factor / bqr_apply
+// two-level form (qr_outer.cu): 256-column outer blocks, their trailing updates and the
+// applications of Q on the tensor cores; used by bqr_factor / bqr_apply when bqr_outer_used
+// Where a QR or an application of Q sits in the pipeline: the automatic choice takes the
+// tensor cores only where the operands are scaled column by column (the preconditioner's A P,
+// U = Q [U_R; 0]); the switch's QR of B (rows graded like X) stays on the FP64 pipe.
+enum QrSite { kQrSitePrecond = 0, kQrSiteSwitch = 1, kQrSiteFinal = 2, kQrSiteCall = 3 };
+constexpr int kQrOuterMinNFactor = 6144;  // automatic choice: preconditioner QR from this n on
+constexpr int kQrOuterMinNApply = 4096;   // automatic choice: U assembly / standalone from this n on
+bool bqr_outer_used(const mpjsvd_ctx* h, int m, int n, int site);
+size_t bqr_outer_ws_bytes(int m, int n);           // its scratch (bytes)
+// scratch bytes bqr_factor / bqr_apply need for m rows and n columns (or reflectors), any site
+size_t bqr_ws_bytes(const mpjsvd_ctx* h, int m, int n);
+int bqr_factor_outer(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, void* W, DevState* st,
+                     int gate_want);
+int bqr_apply_outer(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau, double* C,
+                    int ldc, bool ident, void* W, DevState* st, int gate_want);
+struct GemmArgs;
+int launch_gemm_d(mpjsvd_ctx* h, const GemmArgs& g, const int* gate, int want);  // binary64 SIMT product
 int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
-               int gate_want);
+               int gate_want, int site = kQrSiteCall);
 int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,
-              double* C, int ldc, bool ident, double* W, DevState* st, int gate_want);
+              double* C, int ldc, bool ident, double* W, DevState* st, int gate_want, int site = kQrSiteCall);
 // binary32 pivot search of Alg. 5 (qrcp_low.cu); 1 = does not fit, nothing launched
 int launch_qrcp_low(mpjsvd_ctx* h, int m, int n, const double* A, int lda, int* perm, float* bcast,
                     size_t bcast_bytes, DevState* st);

@@ -174,6 +174,7 @@ struct OzArgs {
     double* C;
     int ldc;
     int klo_from_row, khi_from_row;  // clip the k range of a tile by the triangular structure
+    int sub;                         // C <- C - op(A) B instead of C <- op(A) B
 };
 
 __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(OzArgs g, DevState* st, const int* gate, int want)
@@ -288,7 +289,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(OzArgs g, DevState* s
 #pragma unroll
                 for (int j = 0; j < kOzTN; ++j) {
                     const int col = n0 + j;
-                    if (col < g.N) g.C[(size_t)col * g.ldc + row] = ldexp(acc[j], er + g.eb[col]);
+                    if (col < g.N) {
+                        double* cp = g.C + (size_t)col * g.ldc + row;
+                        const double pv = ldexp(acc[j], er + g.eb[col]);
+                        *cp = g.sub ? *cp - pv : pv;
+                    }
                 }
             }
         }
@@ -350,6 +355,7 @@ int ozaki_dgemm(mpjsvd_ctx* h, const GemmArgs& ga, void* ws, const int* gate, in
     g.Asl = Asl; g.Bsl = Bsl; g.ea = exA; g.eb = exB;
     g.C = (double*)ga.C; g.ldc = ga.ldc;
     g.klo_from_row = ga.klo_from_row ? 1 : 0;
+    g.sub = ga.sub ? 1 : 0;
     g.khi_from_row = ga.khi_from_row ? 1 : 0;
     k_oz_gemm<<<dim3(MB, NB), kOzThreads, kOzSmem, s>>>(g, st, gate, want);
     e = cudaGetLastError();
@@ -371,6 +377,7 @@ int dgemm_tc_call(mpjsvd_ctx* h, int M, int N, int K, const double* A, int lda, 
     g.B = B; g.ldb = ldb; g.transB = false;
     g.C = C; g.ldc = ldc;
     g.klo_from_row = g.khi_from_row = false;
+    g.sub = false;
     return ozaki_dgemm(h, g, h->ws, nullptr, 0, (DevState*)h->dstate);
 }
 

@@ -636,11 +636,21 @@ static int bqr_factor_nb(mpjsvd_ctx* h, int m, int n, double* A, int lda, double
     return 0;
 }
 
-// Householder QR of the m x n (m >= n) column-major A in place (geqrf layout) with tau[n].
-// W: bqr_wbuf_doubles(n, m) doubles of scratch. Requires bqr_nb(m) > 0.
-int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
-               int gate_want)
+// Scratch bytes of bqr_factor / bqr_apply for m rows and n columns (or reflectors).
+size_t bqr_ws_bytes(const mpjsvd_ctx* h, int m, int n)
 {
+    const size_t one = sizeof(double) * bqr_wbuf_doubles(n, m);
+    bool any = false;
+    for (int site = kQrSitePrecond; site <= kQrSiteCall; ++site) any = any || bqr_outer_used(h, m, n, site);
+    return any ? std::max(one, bqr_outer_ws_bytes(m, n)) : one;
+}
+
+// Householder QR of the m x n (m >= n) column-major A in place (geqrf layout) with tau[n].
+// W: bqr_ws_bytes(h, m, n) bytes of scratch. Requires bqr_nb(m) > 0.
+int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, double* W, DevState* st,
+               int gate_want, int site)
+{
+    if (bqr_outer_used(h, m, n, site)) return bqr_factor_outer(h, m, n, A, lda, tau, W, st, gate_want);
     const int nb = bqr_nb(m);
     if (nb == 32) return bqr_factor_nb<32>(h, m, n, A, lda, tau, W, st, gate_want);
     if (nb == 16) return bqr_factor_nb<16>(h, m, n, A, lda, tau, W, st, gate_want);
@@ -650,10 +660,13 @@ int bqr_factor(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau, dou
 // C (m x ncols, leading rows of a matrix with ld ldc) <- Q C, Q = H_0 ... H_{k-1} from the k
 // reflectors stored in V (m x k, geqrf layout). ident: C holds the identity's first ncols
 // columns on entry, so panel p only touches columns >= its first (the structure of forming Q).
-// W: bqr_wbuf_doubles(ncols, m) doubles of scratch.
+// W: bqr_wbuf_doubles(ncols, m) doubles of scratch, or bqr_outer_ws_bytes(m, max(ncols, k))
+// bytes when bqr_outer_used(h, m, k).
 int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, const double* tau,
-              double* C, int ldc, bool ident, double* W, DevState* st, int gate_want)
+              double* C, int ldc, bool ident, double* W, DevState* st, int gate_want, int site)
 {
+    if (bqr_outer_used(h, m, k, site))
+        return bqr_apply_outer(h, m, ncols, k, V, ldv, tau, C, ldc, ident, W, st, gate_want);
     constexpr int NB = 32;
     const WySet ws = wyset_at(W + wyset_doubles(32, m, kWyRcNarrow), ncols, m, kWyRc);
     cudaError_t e = cudaMemsetAsync(ws.cnt, 0, wyset_cnt_bytes(ncols), h->stream);
@@ -672,7 +685,7 @@ int bqr_apply(mpjsvd_ctx* h, int m, int ncols, int k, const double* V, int ldv, 
 
 int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau)
 {
-    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(n, m);
+    const size_t wbytes = bqr_ws_bytes(h, m, n);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;
@@ -685,7 +698,8 @@ int qr_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, double* tau)
 int apply_q_call(mpjsvd_ctx* h, int m, int ncols, int k, const double* A, int lda, const double* tau,
                  double* C, int ldc)
 {
-    const size_t wbytes = sizeof(double) * bqr_wbuf_doubles(ncols, m);
+    size_t wbytes = sizeof(double) * bqr_wbuf_doubles(ncols, m);
+    if (bqr_outer_used(h, m, k, kQrSiteCall)) wbytes = std::max(wbytes, bqr_outer_ws_bytes(m, std::max(ncols, k)));
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, wbytes);
     if (rc) return rc;
     DevState* st = (DevState*)h->dstate;

@@ -525,7 +525,8 @@ enum {
 };
 static_assert(L_COUNT <= 40, "SingleLayout::off is too small");
 
-static SingleLayout single_layout(int m, int n, bool qr_first, bool lq, bool oz)
+// wy: scratch bytes of the blocked QRs and their applications (bqr_ws_bytes for m rows, n columns)
+static SingleLayout single_layout(int m, int n, bool qr_first, bool lq, bool oz, size_t wy)
 {
     size_t nn = (size_t)n * n;
     int mq = qr_first ? n : m;
@@ -560,7 +561,7 @@ static SingleLayout single_layout(int m, int n, bool qr_first, bool lq, bool oz)
                            qrcp_low_bcast_bytes(qr_first ? n : m, n, kMaxGroupCtas));
     sz[L_FLAGS] = sizeof(int) * n;
     sz[L_VER] = sizeof(unsigned) * 2 * ((size_t)n + 2);  // 2 * sweep_blocks(n, w) for any w
-    sz[L_WY] = sizeof(double) * bqr_wbuf_doubles(n, m);
+    sz[L_WY] = wy;
     sz[L_LQ] = lq ? sizeof(double) * nn : 0;   // the QR of R^T (second preconditioning)
     sz[L_TAUQ] = lq ? sizeof(double) * n : 0;
     sz[L_OZ] = oz ? ozaki_ws_bytes(n, n, n) : 0;  // split operands of the tensor-core GEMMs
@@ -683,7 +684,7 @@ static int launch_apply_q(mpjsvd_ctx* h, int mrows, int ncols, int k, const doub
     return 0;
 }
 
-static int launch_gemm_d(mpjsvd_ctx* h, const GemmArgs& g, const int* gate, int want)
+int launch_gemm_d(mpjsvd_ctx* h, const GemmArgs& g, const int* gate, int want)
 {
     const int tiles = ((g.M + kDgBM - 1) / kDgBM) * ((g.N + kDgBN - 1) / kDgBN);
     k_dgemm<<<tiles, kDgThreads, 0, h->stream>>>(g, gate, want);
@@ -708,7 +709,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     // operand splitting, or on the FP64 pipe
     const bool oz = P.gemm_kernel == MPJSVD_GEMMK_TC ||
                     (P.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN && n <= kGemmTcMaxN);
-    SingleLayout L = single_layout(m, n, qr_first, lq, oz);
+    SingleLayout L = single_layout(m, n, qr_first, lq, oz, bqr_ws_bytes(h, m, n));
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;
     char* base = (char*)h->ws;
@@ -775,7 +776,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     if (qr_first) {
         k_copy_check<<<egrid, T256, 0, s>>>(m, n, A, lda, W0, m, st); ++h->launch_count;
         if (blocked_m) {
-            if ((rc = bqr_factor(h, m, n, W0, m, tau0, wy, st, -1))) return rc;
+            if ((rc = bqr_factor(h, m, n, W0, m, tau0, wy, st, -1, kQrSitePrecond))) return rc;
         } else {
             if ((rc = launch_hhqr(h, false, m, n, W0, m, tau0, perm2, st, -1, bcast, qflags))) return rc;
         }
@@ -794,7 +795,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         if (rc < 0) return rc;
         if (rc == 0) {
             k_gather_cols<<<std::min(n, egrid), T256, 0, s>>>(mq, n, Wq, mq, perm, WqL, mq, st); ++h->launch_count;
-            if ((rc = bqr_factor(h, mq, n, WqL, mq, tau, wy, st, -1))) return rc;
+            if ((rc = bqr_factor(h, mq, n, WqL, mq, tau, wy, st, -1, kQrSitePrecond))) return rc;
             mixed_done = true;
         }
     }
@@ -809,7 +810,7 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         k_lq_decide<<<std::max(1, std::min(egrid, (n * 32 + T256 - 1) / T256)), T256, 0, s>>>(
             n, WqL, mq, P.precond == MPJSVD_PRECOND_L ? 1 : 0, st); ++h->launch_count;
         k_rt_copy<<<egrid, T256, 0, s>>>(n, WqL, mq, Lq, st); ++h->launch_count;
-        if ((rc = bqr_factor(h, n, n, Lq, n, tauq, wy, st, kGateLq + 1))) return rc;
+        if ((rc = bqr_factor(h, n, n, Lq, n, tauq, wy, st, kGateLq + 1, kQrSiteSwitch))) return rc;
     }
     k_form_x<<<egrid, T256, 0, s>>>(n, WqL, mq, Lq, X, P.precond, st); ++h->launch_count;
     h->last_precond = P.precond;
@@ -894,9 +895,9 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
             if ((rc = launch_sweeps_f32v(h, Dl, Xl, Bq, st, 0, 1))) return rc;
             record(h, 3);
             // ---- [3.3] the alternative switch: V_low = Q R2, V_acc = Q, Y = X Q
-            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
+            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1, kQrSiteSwitch))) return rc;
             k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
-            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
+            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1, kQrSiteSwitch))) return rc;
             GemmArgs g2;
             g2.M = n; g2.N = n; g2.K = n;
             g2.A = X; g2.lda = n; g2.transA = false;
@@ -922,9 +923,9 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
             g.klo_from_row = x_lower;  // X^T upper when X lower
             g.khi_from_row = x_upper;
             if ((rc = gemm64(g, &st->gate_low, 1))) return rc;
-            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1))) return rc;
+            if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, 1, kQrSiteSwitch))) return rc;
             k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, 1); ++h->launch_count;
-            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1))) return rc;
+            if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, 1, kQrSiteSwitch))) return rc;
             GemmArgs g2;
             g2.M = n; g2.N = n; g2.K = n;
             g2.A = X; g2.lda = n; g2.transA = false;
@@ -993,9 +994,9 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
         g3.klo_from_row = x_lower;
         g3.khi_from_row = x_upper;
         if ((rc = gemm64(g3, nullptr, 0))) return rc;
-        if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, -1))) return rc;
+        if ((rc = bqr_factor(h, n, n, Bq, n, tau2, wy, st, -1, kQrSiteSwitch))) return rc;
         k_identity<<<egrid, T256, 0, s>>>(n, Vacc, st, -1); ++h->launch_count;
-        if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, -1))) return rc;
+        if ((rc = bqr_apply(h, n, n, n, Bq, n, tau2, Vacc, n, true, wy, st, -1, kQrSiteSwitch))) return rc;
         GemmArgs g4;
         g4.M = n; g4.N = n; g4.K = n;
         g4.A = X; g4.lda = n; g4.transA = false;
@@ -1012,21 +1013,21 @@ int svd_single(mpjsvd_ctx* h, int m, int n, const double* A, int lda, double* U,
     k_rank_desc<double><<<(n + T256 - 1) / T256, T256, 0, s>>>(n, sig, ord2, st, -1); ++h->launch_count;
     if (lq) {
         // X = L = R Q': R = U_X Sigma (Q' V_acc)^T, so V_R = Q' V_acc
-        if ((rc = bqr_apply(h, n, n, n, Lq, n, tauq, Vacc, n, false, wy, st, kGateLq + 1))) return rc;
+        if ((rc = bqr_apply(h, n, n, n, Lq, n, tauq, Vacc, n, false, wy, st, kGateLq + 1, kQrSiteSwitch))) return rc;
     }
     k_finalize<<<std::min(n, egrid), T256, 0, s>>>(m, n, Y, Vacc, sig, ord2, perm,
                                                     lq ? MPJSVD_PRECOND_R : P.precond, U, S, V, st); ++h->launch_count;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("finalize kernels", e);
     if (qr_first) {
-        if ((rc = bqr_apply(h, n, n, n, WqL, n, tau, U, m, false, wy, st, -1))) return rc;
+        if ((rc = bqr_apply(h, n, n, n, WqL, n, tau, U, m, false, wy, st, -1, kQrSiteFinal))) return rc;
         if (blocked_m) {
-            if ((rc = bqr_apply(h, m, n, n, W0, m, tau0, U, m, false, wy, st, -1))) return rc;
+            if ((rc = bqr_apply(h, m, n, n, W0, m, tau0, U, m, false, wy, st, -1, kQrSiteFinal))) return rc;
         } else {
             if ((rc = launch_apply_q(h, m, n, n, W0, m, tau0, U, m, false, st, -1))) return rc;
         }
     } else if (blocked_m) {
-        if ((rc = bqr_apply(h, m, n, n, WqL, m, tau, U, m, false, wy, st, -1))) return rc;
+        if ((rc = bqr_apply(h, m, n, n, WqL, m, tau, U, m, false, wy, st, -1, kQrSiteFinal))) return rc;
     } else {
         if ((rc = launch_apply_q(h, m, n, n, WqL, m, tau, U, m, false, st, -1))) return rc;
     }
@@ -1041,7 +1042,7 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
     const size_t sz_tmp = align256(sizeof(double) * (size_t)m * n);
     const size_t sz_bc = align256(std::max(sizeof(double) * (size_t)std::max(m, n) * (size_t)std::max(n, 2 * kMaxGroupCtas),
                                            qrcp_low_bcast_bytes(m, n, kMaxGroupCtas)));
-    const size_t sz_wy = align256(sizeof(double) * bqr_wbuf_doubles(n, m));
+    const size_t sz_wy = align256(bqr_ws_bytes(h, m, n));
     const size_t sz_fl = align256(sizeof(int) * (size_t)n);
     int rc = ensure_buffer(&h->ws, &h->ws_bytes, sz_tmp + sz_bc + sz_wy + sz_fl);
     if (rc) return rc;
@@ -1062,7 +1063,7 @@ int geqp3_call(mpjsvd_ctx* h, int m, int n, double* A, int lda, int* jpvt, doubl
         if (rc < 0) return rc;
         if (rc == 0) {
             k_gather_cols<<<std::min(n, egrid), 256, 0, s>>>(m, n, A, lda, jpvt, tmp, m, st); ++h->launch_count;
-            if ((rc = bqr_factor(h, m, n, tmp, m, tau, wy, st, -1))) return rc;
+            if ((rc = bqr_factor(h, m, n, tmp, m, tau, wy, st, -1, kQrSitePrecond))) return rc;
             mixed_done = true;
         }
     }
@@ -1183,7 +1184,8 @@ static int svd_noalloc(int m, int n, const double* A, int lda, double* U, double
                                       ctx.params.precond >= MPJSVD_PRECOND_L,
                                       ctx.params.gemm_kernel == MPJSVD_GEMMK_TC ||
                                           (ctx.params.gemm_kernel == MPJSVD_GEMMK_AUTO && n >= kGemmTcMinN &&
-                                           n <= kGemmTcMaxN)).total;
+                                           n <= kGemmTcMaxN),
+                                      bqr_ws_bytes(&ctx, m, n)).total;
     if (state_bytes + need > kNoAllocBytes)
         return cuda_fail("mpjsvd_svd_noalloc: workspace exceeds the static scratch",
                          cudaErrorInvalidValue);

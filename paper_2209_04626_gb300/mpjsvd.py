@@ -25,6 +25,7 @@ LOWK = {"auto": 0, "tc": 1, "reg": 2}
 SWITCH = {"u": 0, "v": 1}
 GEMMK = {"auto": 0, "tc": 1, "f64": 2}
 WORKK = {"auto": 0, "cluster": 1, "cta": 2}
+QRU = {"auto": 0, "tc": 1, "f64": 2}
 BRANCH = {0: "mixed", 1: "skip_cond", 2: "skip_trailing", 3: "skip_orth", 4: "plain", -1: "?"}
 STATUS_NOT_CONVERGED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_ZERO_SIGMA = 1, 2, 4, 8
 
@@ -44,7 +45,7 @@ class Params(ctypes.Structure):
                 ("qrcp", ctypes.c_int), ("stop", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("low_kernel", ctypes.c_int), ("v_by_qr", ctypes.c_int),
                 ("switch_method", ctypes.c_int), ("gemm_kernel", ctypes.c_int), ("y_tol", ctypes.c_double),
-                ("work_kernel", ctypes.c_int), ("work_cluster", ctypes.c_int)]
+                ("work_kernel", ctypes.c_int), ("work_cluster", ctypes.c_int), ("qr_update", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -135,6 +136,8 @@ def mpjsvd_default_params(**overrides):
             v = GEMMK[v]
         if k == "work_kernel" and isinstance(v, str):
             v = WORKK[v]
+        if k == "qr_update" and isinstance(v, str):
+            v = QRU[v]
         setattr(p, k, v)
     return p
 
@@ -295,6 +298,8 @@ class Handle:
                 v = GEMMK[v]
             if k == "work_kernel" and isinstance(v, str):
                 v = WORKK[v]
+            if k == "qr_update" and isinstance(v, str):
+                v = QRU[v]
             setattr(self.params, k, v)
         mpjsvd_set_params(self.h, self.params)
 
