@@ -71,10 +71,11 @@ def test_apply_q_two_level(m, n):
 
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
 def test_svd_with_two_level_qr_against_oracle(mode):
-    """700 x 600, sigma over 5 decades: every QR and application of Q in the pipeline (the
-    preconditioner's, the switch's, U) in the two-level form."""
+    """420 x 300 (an outer block of 256 columns and a ragged one of 44), sigma over 5 decades:
+    every QR and application of Q in the pipeline (the preconditioner's, the switch's, U) in
+    the two-level form."""
     rng = np.random.default_rng(21)
-    A = inputs.known_sigma(rng, 700, 600, np.logspace(0, -5, 600))
+    A = inputs.known_sigma(rng, 420, 300, np.logspace(0, -5, 300))
     U, S, V, st = gpu_svd(A, mode=mode, qr_update="tc")
     assert st["status"] == 0, st
     check_factorization(A, U, S, V)
