@@ -594,7 +594,10 @@ def ours(args):
                                         else "register-resident level-1 visits")},
             "phases_ms": phases,
             "sweeps": {"low": st["sweeps_low"], "work": st["sweeps_work"],
-                       "rot_low": st["rot_low"], "rot_work": st["rot_work"]},
+                       "rot_low": st["rot_low"], "rot_work": st["rot_work"],
+                       "rot_per_sweep_low": st["rot_sweep_low"][:min(16, st["sweeps_low"])],
+                       "rot_per_sweep_work": st["rot_sweep_work"][:min(16, st["sweeps_work"])],
+                       "max_cos_per_sweep_work": st["cos_sweep_work"][:min(16, st["sweeps_work"])]},
             "fp64_gflops_whole_svd": flops_svd_fp64(m, n, st["sweeps_work"], st["rot_work"]) /
             (total_ms / args.steps) / 1e6,
             "compare": compare,

@@ -195,6 +195,12 @@ typedef struct {
                              (pairs with |s_i - s_j| <= gap_tol max(s_i, s_j) plus s_i <= 2^-53 s_0);
                              -1 if the handle has run none */
     int work_cluster;     /* CTAs per visit of the binary64 sweeps (1: one CTA per visit) */
+    /* per sweep (the first 16 of each stage): rotations, and the largest cosine |gamma| /
+       (|x_a| |x_b|) among the rotated pairs (0 when none rotated) */
+    long long rot_sweep_low[16];
+    long long rot_sweep_work[16];
+    float cos_sweep_low[16];
+    float cos_sweep_work[16];
 } mpjsvd_stats;
 
 /* Fill *p with the defaults. Returns 0, or -1 if p is NULL. */

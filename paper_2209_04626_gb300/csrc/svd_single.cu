@@ -1101,6 +1101,13 @@ int read_stats(mpjsvd_ctx* h, mpjsvd_stats* out)
     r.block_w_low = st.branch == 0 ? h->last_block_w_low : 0;
     r.block_w_work = h->last_block_w_work;
     r.work_cluster = h->last_work_cs;
+    for (int s = 0; s < 16; ++s) {
+        r.rot_sweep_low[s] = s < st.sweeps_low ? (long long)st.rot_sweep[0][s] : 0;
+        r.rot_sweep_work[s] = s < st.sweeps_work ? (long long)st.rot_sweep[1][s] : 0;
+        unsigned cl = s < st.sweeps_low ? st.mx_cos[0][s] : 0u, cw = s < st.sweeps_work ? st.mx_cos[1][s] : 0u;
+        memcpy(&r.cos_sweep_low[s], &cl, sizeof(float));
+        memcpy(&r.cos_sweep_work[s], &cw, sizeof(float));
+    }
     r.launches = h->launch_count;
     r.qrcp = h->last_qrcp;
     r.precond = h->last_precond >= MPJSVD_PRECOND_L ? (st.gate_lq ? MPJSVD_PRECOND_L : MPJSVD_PRECOND_R)

@@ -58,10 +58,14 @@ class Stats(ctypes.Structure):
                 ("ms_switch", ctypes.c_float), ("ms_work", ctypes.c_float),
                 ("ms_final", ctypes.c_float), ("launches", ctypes.c_int), ("qrcp", ctypes.c_int),
                 ("precond", ctypes.c_int), ("sweeps_v", ctypes.c_int), ("rot_v", ctypes.c_longlong),
-                ("y2_cols", ctypes.c_int), ("n_flagged", ctypes.c_int), ("work_cluster", ctypes.c_int)]
+                ("y2_cols", ctypes.c_int), ("n_flagged", ctypes.c_int), ("work_cluster", ctypes.c_int),
+                ("rot_sweep_low", ctypes.c_longlong * 16), ("rot_sweep_work", ctypes.c_longlong * 16),
+                ("cos_sweep_low", ctypes.c_float * 16), ("cos_sweep_work", ctypes.c_float * 16)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
+        for name in ("rot_sweep_low", "rot_sweep_work", "cos_sweep_low", "cos_sweep_work"):
+            d[name] = list(d[name])
         d["branch_name"] = BRANCH.get(d["branch"], "?")
         return d
 

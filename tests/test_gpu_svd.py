@@ -256,3 +256,19 @@ def test_switch_comparison():
     (Su, stu), (Sv, stv) = res["u"], res["v"]
     assert np.max(np.abs(Su - Sv) / Su) <= 1e-12
     assert stu["rot_work"] <= stv["rot_work"], (stu["rot_work"], stv["rot_work"])
+
+
+def test_per_sweep_records():
+    """The per-sweep records of both stages add up to the totals, every recorded cosine is in
+    [0, 1], and the last binary64 sweep's rotations are negligible (the stopping rule)."""
+    A, _ = inputs.plain_256x128()
+    U, S, V, st = gpu_svd(A, "mixed")
+    assert st["status"] == 0
+    sl, sw = st["sweeps_low"], st["sweeps_work"]
+    assert 0 < sl <= 16 and 0 < sw <= 16
+    assert sum(st["rot_sweep_low"][:sl]) == st["rot_low"] and sum(st["rot_sweep_work"][:sw]) == st["rot_work"]
+    assert all(v == 0 for v in st["rot_sweep_work"][sw:]) and all(v == 0 for v in st["rot_sweep_low"][sl:])
+    cw = st["cos_sweep_work"][:sw]
+    assert all(0.0 <= c <= 1.0 for c in cw) and all(0.0 <= c <= 1.0 for c in st["cos_sweep_low"][:sl])
+    n = A.shape[1]
+    assert cw[-1] < np.sqrt(n) * np.sqrt(n) * 2.0 ** -53 or st["rot_sweep_work"][sw - 1] == 0
