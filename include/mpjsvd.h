@@ -58,7 +58,9 @@ extern "C" {
 #define MPJSVD_STATUS_OK 0
 #define MPJSVD_STATUS_NOT_CONVERGED 1  /* a Jacobi stage hit maxsweep sweeps */
 #define MPJSVD_STATUS_NONFINITE 2      /* A contains Inf or NaN; outputs are not meaningful */
-#define MPJSVD_STATUS_TIMEOUT 4        /* a bounded device wait gave up; outputs not meaningful */
+#define MPJSVD_STATUS_TIMEOUT 4        /* a bounded device wait gave up (or a kernel found its launch
+                                          geometry not the one it was launched for); outputs not
+                                          meaningful */
 #define MPJSVD_STATUS_ZERO_SIGMA 8     /* some singular value is exactly zero (rank deficient) */
 
 /* Algorithm choices. */

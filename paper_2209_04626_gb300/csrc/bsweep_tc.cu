@@ -170,11 +170,11 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
         cp_async_commit();
     }
     for (int ch = 0; ch < nch; ++ch) {
-        const int nx = ch + kGramStages - 1;
-        if (nx < nch) gram_issue(X, ldX, mX, s, nx, vec, rawb + (size_t)(nx % kGramStages) * kGramRaw);
-        cp_async_commit();
         const int buf = ch & 1;
-        cp_async_wait<kGramStages - 1>();  // this thread's copies of chunk ch have landed
+        // this thread's copies of chunk ch have landed (groups of chunks ch + 1 .. ch + 6 may
+        // still be in flight: the copies of chunk ch + 7 are issued after this chunk's split,
+        // so the proxy fence below never waits for a copy issued in this iteration)
+        cp_async_wait<kGramStages - 2>();
         if (!drain1(s, buf, st)) {  // MMAs of chunk ch - 2 have read the buffer
             cp_async_wait_all();
             return false;
@@ -220,6 +220,9 @@ __device__ bool gram_tf32(const float* X, int ldX, int mX, BVisitShared& s, unsi
             ++s.pend[buf];
         }
         MPJ_TC_PROBE(6)
+        const int nx = ch + kGramStages - 1;  // its stage was read in iteration ch - 1
+        if (nx < nch) gram_issue(X, ldX, mX, s, nx, vec, rawb + (size_t)(nx % kGramStages) * kGramRaw);
+        cp_async_commit();
     }
     cp_async_wait_all();  // (only empty groups remain) before G overwrites the raw stages
     if (!drain1(s, 0, st) || !drain1(s, 1, st)) return false;

@@ -387,6 +387,15 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x;
     ClPar par;
+    // The launch geometry this kernel is written for: clusters of exactly CS consecutive CTAs
+    // of a one-dimensional grid, the rank equal to blockIdx.x mod CS, at most kClMaxThreads
+    // threads. The same for every CTA of a cluster (so all leave together), checked before any
+    // access to a peer's shared memory; a mismatch is recorded and nothing is computed.
+    if (cl.num_blocks() != (unsigned)CS || gridDim.x % CS != 0 || gridDim.y != 1 || gridDim.z != 1 ||
+        rank != (int)(blockIdx.x % CS) || blockDim.x > kClMaxThreads || blockDim.y != 1 || blockDim.z != 1) {
+        if (tid == 0) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+        return;
+    }
     cl.sync();  // every CTA of the cluster has started before any writes a peer's shared memory
     // the gate and the failure flag: every CTA of the cluster leaves, or none
     if (!cl_agree<W, CS>(cl, sm, par, rank, !call_failed(st) && gate_open(st, gate_want), 0, nullptr)) return;
