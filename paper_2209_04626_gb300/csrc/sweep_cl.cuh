@@ -44,11 +44,28 @@ constexpr int kClMaxThreads = 256;
 __host__ __device__ constexpr int cl_rpt(int w) { return 32 / w; }
 __host__ __device__ constexpr int cl_rows_per_cta(int w) { return cl_rpt(w) * kClMaxThreads; }
 
+// The batched test of a visit (sweeps whose rotations have become rare): the values it reduces,
+// in this order: the 2W squared norms and the W (W - 1) intra-block pairs (first round of a
+// sweep only), then the W^2 cross pairs, each pair as the sequential inner rounds take it.
+template <int W>
+struct ClBatch {
+    static constexpr int NI = (W - 1) * W;
+    static constexpr int NC = W * W;
+    static constexpr int NF = 2 * W + NI + NC;
+};
+// A sweep takes the batched test when the previous one rotated no pair with a cosine above
+// this (the next sweep's rotations are then of the order of its square: almost no visit
+// rotates).
+constexpr float kClBatchCos = 1e-6f;
+
 template <int W, int CS>
 struct ClShared {
     VisitShared<double, W> v;   // the visit's state: identical in every CTA of the cluster
     double xch[2][CS][2 * W];   // partial sums of each rank (double-buffered by exchange parity)
     int agree[2][CS][2];        // per rank: ok flag, rank 0's value (parity-buffered)
+    double bpart[ClBatch<W>::NF][kClMaxThreads / 32];  // batched test: per-warp partial sums
+    double xchb[2][CS][ClBatch<W>::NF];                // batched test: each rank's partial sums
+    int brot;                                           // batched test: pairs that would rotate
 };
 
 // Parities of the two exchange buffers. Every CTA of a cluster runs the same sequence of
@@ -57,6 +74,7 @@ struct ClShared {
 struct ClPar {
     int x = 0;
     int a = 0;
+    int b = 0;
 };
 
 // Every CTA contributes ok; afterwards every thread of every CTA of the cluster holds the AND
@@ -224,12 +242,113 @@ __device__ __forceinline__ void cl_inner_round(const cg::cluster_group& cl, doub
     }
 }
 
+// Columns (a, b) of value idx of the batched test (FIRST: norms, intra pairs, cross pairs; else
+// cross pairs only). Compile-time in the unrolled loops below.
+template <bool FIRST, int W>
+__device__ __forceinline__ constexpr int batch_a(int idx)
+{
+    return (FIRST && idx < 2 * W) ? idx
+         : (FIRST && idx < 2 * W + ClBatch<W>::NI) ? pair_a<W>(true, (idx - 2 * W) / W, (idx - 2 * W) % W)
+         : pair_a<W>(false, (idx - (FIRST ? 2 * W + ClBatch<W>::NI : 0)) / W,
+                     (idx - (FIRST ? 2 * W + ClBatch<W>::NI : 0)) % W);
+}
+template <bool FIRST, int W>
+__device__ __forceinline__ constexpr int batch_b(int idx)
+{
+    return (FIRST && idx < 2 * W) ? idx
+         : (FIRST && idx < 2 * W + ClBatch<W>::NI) ? pair_b<W>(true, (idx - 2 * W) / W, (idx - 2 * W) % W)
+         : pair_b<W>(false, (idx - (FIRST ? 2 * W + ClBatch<W>::NI : 0)) / W,
+                     (idx - (FIRST ? 2 * W + ClBatch<W>::NI : 0)) % W);
+}
+
+// Per-warp partial sums of values OFF .. OFF + REM - 1 into bpart, at most 16 at a time (the
+// rows stay in registers; only one chunk of sums is live).
+template <bool FIRST, int OFF, int REM, int W, int RPT, int CS>
+__device__ __forceinline__ void cl_batch_parts(const double (&x)[RPT][2 * W], ClShared<W, CS>& sm, int lane, int wid)
+{
+    if constexpr (REM > 0) {
+        constexpr int C = REM >= 16 ? 16 : (REM >= 8 ? 8 : (REM >= 4 ? 4 : (REM >= 2 ? 2 : 1)));
+        double t[C];
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const int a = batch_a<FIRST, W>(OFF + i), b = batch_b<FIRST, W>(OFF + i);
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) acc = fma(x[k][a], x[k][b], acc);
+            t[i] = acc;
+        }
+        warp_reduce_multi<C>(t, lane);
+        constexpr int sh = 5 - ilog2c(C);
+        if ((lane & ((1 << sh) - 1)) == 0) sm.bpart[OFF + (lane >> sh)][wid] = t[0];
+        cl_batch_parts<FIRST, OFF + C, REM - C, W, RPT, CS>(x, sm, lane, wid);
+    }
+}
+
+// The batched test of a visit: every pair's dot product from the unrotated columns (and, in
+// the first round of a sweep, the fresh squared norms, written to sm.v.alpha), summed over the
+// cluster in one exchange, then the rotation test of the inner rounds on all of them. True
+// (every CTA alike) when no pair would rotate. Ends synchronized.
+template <bool FIRST, int W, int RPT, int CS>
+__device__ bool cl_batch_quiet(const cg::cluster_group& cl, const double (&x)[RPT][2 * W], ClShared<W, CS>& sm,
+                               ClPar& par, int rank, double tol2)
+{
+    using B = ClBatch<W>;
+    constexpr int NV = FIRST ? B::NF : B::NC;
+    constexpr int OC = FIRST ? 2 * W + B::NI : 0;
+    VisitShared<double, W>& s = sm.v;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    cl_batch_parts<FIRST, 0, NV, W, RPT, CS>(x, sm, lane, wid);
+    __syncthreads();
+    if (tid < 32) {
+        for (int i = lane; i < NV; i += 32) {
+            const double sv = short_sum(sm.bpart[i], nw);
+#pragma unroll
+            for (int rr = 0; rr < CS; ++rr) *cl.map_shared_rank(&sm.xchb[par.b][rank][i], rr) = sv;
+        }
+    }
+    cl.sync();
+    if (tid < 32) {
+        auto total = [&](int i) {
+            double t = sm.xchb[par.b][0][i];
+#pragma unroll
+            for (int rr = 1; rr < CS; ++rr) t += sm.xchb[par.b][rr][i];
+            return t;
+        };
+        if (FIRST && lane < 2 * W) {
+            const double dc = s.d[lane];
+            s.alpha[lane] = (s.gidx[lane] >= 0) ? total(lane) * dc * dc : 0.0;
+        }
+        __syncwarp();
+        int cnt = 0;
+        for (int i = lane; i < NV - (FIRST ? 2 * W : 0); i += 32) {
+            const int idx = i + (FIRST ? 2 * W : 0);
+            int a, b;
+            if (FIRST && idx < OC) {
+                a = pair_a<W>(true, (idx - 2 * W) / W, (idx - 2 * W) % W);
+                b = pair_b<W>(true, (idx - 2 * W) / W, (idx - 2 * W) % W);
+            } else {
+                a = pair_a<W>(false, (idx - OC) / W, (idx - OC) % W);
+                b = pair_b<W>(false, (idx - OC) / W, (idx - OC) % W);
+            }
+            if (s.gidx[a] >= 0 && s.gidx[b] >= 0 && (!s.cross_only || s.side[a] != s.side[b])) {
+                const double gamma = total(idx) * (s.d[a] * s.d[b]);
+                if (above_tol<double>(gamma, s.alpha[a], s.alpha[b], 0.0, tol2)) ++cnt;
+            }
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) sm.brot = cnt;
+    }
+    par.b ^= 1;
+    __syncthreads();
+    return sm.brot == 0;
+}
+
 // X part of a visit on this CTA's rows: load, rotate, store. Rank 0 stores the columns' scales
 // and tracked norms. Returns the rotation count (the same in every CTA). Ends with a CTA
 // barrier after this CTA's stores.
 template <int W, int RPT, int CS>
 __device__ int cl_visit_x(const cg::cluster_group& cl, const SweepDims& D, double* X, int bi, int bj, bool first,
-                          ClShared<W, CS>& sm, ClPar& par, int rank, ClRows rows)
+                          ClShared<W, CS>& sm, ClPar& par, int rank, ClRows rows, bool batch)
 {
     VisitShared<double, W>& s = sm.v;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -275,7 +394,20 @@ __device__ int cl_visit_x(const cg::cluster_group& cl, const SweepDims& D, doubl
             x[k][c] = (gc >= 0 && r < rows.hi) ? __ldcg(col + r) : 0.0;
         }
     }
-    if (first) cl_norms<W, RPT, CS>(cl, x, sm, par, rank);
+    bool fresh = false;  // the first round's norms already in s.alpha
+    if (batch) {
+        // rotations have become rare: test every pair of the visit at once; a visit without a
+        // rotation stores nothing but the fresh norms
+        const bool quiet = first ? cl_batch_quiet<true, W, RPT, CS>(cl, x, sm, par, rank, tol2)
+                                 : cl_batch_quiet<false, W, RPT, CS>(cl, x, sm, par, rank, tol2);
+        if (quiet) {
+            if (first && rank == 0 && tid < W2 && s.gidx[tid] >= 0) alph[s.gidx[tid]] = s.alpha[tid];
+            __syncthreads();
+            return 0;
+        }
+        fresh = first;
+    }
+    if (first && !fresh) cl_norms<W, RPT, CS>(cl, x, sm, par, rank);
 
     if (first) {
 #pragma unroll
@@ -424,6 +556,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     unsigned* vv = D.ver + k;
     int sweep = 0;
     bool conv = false;
+    bool batch = false;  // the batched test (agreed with the convergence decision of the previous sweep)
     for (; sweep < D.maxsweep; ++sweep) {
         for (long long f = cid; f < per_sweep; f += ncl) {
             const int r = (int)(f / half), i = (int)(f - (long long)r * half);
@@ -432,7 +565,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
             if (bi > bj) { const int t = bi; bi = bj; bj = t; }
             const unsigned R = (unsigned)(sweep * rounds + r);
             if (!cl_agree<W, CS>(cl, sm, par, rank, cl_wait_local(D.ver, bi, bj, R, st), 0, nullptr)) return;
-            const int nrot = cl_visit_x<W, RPT, CS>(cl, D, X, bi, bj, r == 0, sm, par, rank, xr);
+            const int nrot = cl_visit_x<W, RPT, CS>(cl, D, X, bi, bj, r == 0, sm, par, rank, xr, batch);
             if (tid == 0) __threadfence();  // this CTA's stores before the barrier below
             // V's versions (each CTA acquires them for itself) and the release of X: after this
             // barrier every rank's X stores precede rank 0's release
@@ -462,11 +595,14 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
         }
         const bool ok = g.sync();
         int c0 = 0;
-        if (rank == 0 && tid == 0)
+        if (rank == 0 && tid == 0) {
             c0 = (__ldcg(&rot_sweep[sweep]) == 0 || negligible_sweep(D, mxc, mxt, sweep)) ? 1 : 0;
+            if (__uint_as_float(__ldcg(mxc + sweep)) < kClBatchCos) c0 |= 2;
+        }
         int cdec = 0;
         if (!cl_agree<W, CS>(cl, sm, par, rank, ok, c0, &cdec)) return;
-        if (cdec) {
+        batch = (cdec & 2) != 0;
+        if (cdec & 1) {
             conv = true;
             ++sweep;
             break;
