@@ -64,6 +64,9 @@ class _Variant:
         L.orc_jacobi.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, ctypes.c_int,
                                  ctypes.c_int, creal, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_jacobi_derijk.argtypes = [ctypes.c_int, ctypes.c_int, rp, ctypes.c_int, rp, ctypes.c_int,
+                                        ctypes.c_int, creal, ctypes.c_int, ctypes.c_int, _ip, _ip,
+                                        ctypes.POINTER(ctypes.c_longlong)]
         L.orc_jacobi_f32.argtypes = [ctypes.c_int, ctypes.c_int, _fp, ctypes.c_int, _fp, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _ip,
                                      ctypes.POINTER(ctypes.c_longlong)]
@@ -202,6 +205,24 @@ def jacobi(X, V=None, tol=None, maxsweep=30, ext=False, stop=0):
                         V.shape[0] if V is not None else 0, tol, maxsweep, stop, ctypes.byref(sw),
                         ctypes.byref(rot))
     return X, V, sw.value, rot.value, rc
+
+
+def jacobi_derijk(X, V=None, tol=None, maxsweep=30, ext=False, stop=0):
+    """Alg. 1 with de Rijk's pivoting (Section 2.1) in the working precision on a copy of X;
+    returns (X_inf, V, perm, sweeps, rotations, rc), perm[j] = the input column in position j."""
+    v = _v(ext)
+    X = v.arr(X).copy(order="F")
+    m, n = X.shape
+    if V is not None:
+        V = v.arr(V).copy(order="F")
+    tol = np.sqrt(m) * unit_roundoff(ext) if tol is None else tol
+    perm = np.zeros(n, dtype=np.int32)
+    sw = ctypes.c_int()
+    rot = ctypes.c_longlong()
+    rc = v.L.orc_jacobi_derijk(m, n, v.ptr(X), m, v.ptr(V), V.shape[0] if V is not None else 1,
+                               V.shape[0] if V is not None else 0, tol, maxsweep, stop,
+                               perm.ctypes.data_as(_ip), ctypes.byref(sw), ctypes.byref(rot))
+    return X, V, perm, sw.value, rot.value, rc
 
 
 def jacobi_f32(X, tol=None, maxsweep=30, stop=0):

@@ -378,6 +378,70 @@ int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv,
     return converged ? 0 : 1;
 }
 
+/* Alg. 1 in binary64 with de Rijk's pivoting (Section 2.1): a sweep is n - 1 subsweeps; subsweep
+ * p first moves the column of largest Euclidean norm among columns p .. n - 1 to position p
+ * (interchanging it with column p, and the same columns of V; the first such column on ties),
+ * then orthogonalizes the pairs (p, q), q = p + 1 .. n - 1, with the same test, rotation and
+ * stopping rules as orc_jacobi. The column order of the result is therefore the one the last
+ * sweep left: descending norms. perm (optional, n entries): perm[j] = the input column now in
+ * position j. */
+int orc_jacobi_derijk(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
+                      int maxsweep, int stop, int* perm, int* sweeps, long long* rotations)
+{
+    long long rot = 0;
+    int sweep = 0, converged = 0;
+    if (perm)
+        for (int j = 0; j < n; ++j) perm[j] = j;
+    while (sweep < maxsweep && !converged) {
+        converged = 1;
+        double cos_max = 0.0, tan_max = 0.0;
+        for (int p = 0; p < n - 1; ++p) {
+            /* the dominant column of X(:, p:n) */
+            int jmax = p;
+            orc_real nmax = -1.0;
+            for (int j = p; j < n; ++j) {
+                orc_real s2 = 0.0;
+                for (int i = 0; i < m; ++i) s2 += AT(X, i, j, ldx) * AT(X, i, j, ldx);
+                if (s2 > nmax) {
+                    nmax = s2;
+                    jmax = j;
+                }
+            }
+            if (jmax != p) {
+                for (int i = 0; i < m; ++i) {
+                    orc_real t = AT(X, i, p, ldx);
+                    AT(X, i, p, ldx) = AT(X, i, jmax, ldx);
+                    AT(X, i, jmax, ldx) = t;
+                }
+                if (V)
+                    for (int i = 0; i < nv; ++i) {
+                        orc_real t = AT(V, i, p, ldv);
+                        AT(V, i, p, ldv) = AT(V, i, jmax, ldv);
+                        AT(V, i, jmax, ldv) = t;
+                    }
+                if (perm) {
+                    int t = perm[p];
+                    perm[p] = perm[jmax];
+                    perm[jmax] = t;
+                }
+            }
+            for (int q = p + 1; q < n; ++q) {
+                if (jacobi_pair(m, &AT(X, 0, p, ldx), &AT(X, 0, q, ldx), V ? &AT(V, 0, p, ldv) : NULL,
+                                V ? &AT(V, 0, q, ldv) : NULL, nv, tol, &cos_max, &tan_max)) {
+                    ++rot;
+                    converged = 0;
+                }
+            }
+        }
+        if (!converged && stop == 0 && sweep > 0 && negligible_sweep(n, (double)tol, cos_max, tan_max))
+            converged = 1;
+        ++sweep;
+    }
+    if (sweeps) *sweeps = sweep;
+    if (rotations) *rotations = rot;
+    return converged ? 0 : 1;
+}
+
 /* Alg. 1 in binary32 without V (the lower-precision stage of Alg. 4). Same steps and
  * stopping rules as orc_jacobi; every operation rounds to binary32. */
 int orc_jacobi_f32(int m, int n, float* X, int ldx, float* V, int ldv, int nv, float tol, int maxsweep,

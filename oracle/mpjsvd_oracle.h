@@ -121,6 +121,13 @@ void orc_apply_q(int trans, int m, int ncols, int k, const orc_real* V, int ldv,
 int orc_jacobi(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
                int maxsweep, int stop, int* sweeps, long long* rotations);
 
+/* Alg. 1 with de Rijk's pivoting (Section 2.1): subsweep p first moves the column of largest
+ * norm among p .. n - 1 to position p (and the same column of V), then rotates the pairs
+ * (p, q), q > p. perm (optional): perm[j] = the input column in position j at the end. Same
+ * test, rotation, stopping rules and return value as orc_jacobi. */
+int orc_jacobi_derijk(int m, int n, orc_real* X, int ldx, orc_real* V, int ldv, int nv, orc_real tol,
+                      int maxsweep, int stop, int* perm, int* sweeps, long long* rotations);
+
 /* Alg. 1 in binary32 (Alg. 4: "without generating V explicitly"; V (nv x n, binary32) is
  * accumulated only when not NULL, for the alternative switch). */
 int orc_jacobi_f32(int m, int n, float* X, int ldx, float* V, int ldv, int nv, float tol, int maxsweep,

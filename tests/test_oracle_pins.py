@@ -292,6 +292,53 @@ def test_jacobi_f64_and_f32_converge_to_svd():
     assert np.abs(Xn.T @ Xn - np.eye(n)).max() < 1e-5
 
 
+def test_derijk_pivoting_converges_to_the_svd_with_sorted_columns():
+    """Alg. 1 with de Rijk's pivoting (Section 2.1): the same singular values as LAPACK, X V = X_inf
+    with V orthogonal and V P the accumulated permutation, and (by construction: the last sweep
+    rotates nothing and moves the largest remaining column forward in every subsweep) columns
+    in descending norm order."""
+    rng = np.random.default_rng(15)
+    n = 24
+    X = inputs.known_sigma(rng, 30, n, np.logspace(0, -3, n))
+    Xi, V, perm, sw, rot, rc = oracle.jacobi_derijk(X, np.eye(n))
+    assert rc == 0 and sorted(perm.tolist()) == list(range(n))
+    S = np.linalg.norm(Xi, axis=0)
+    assert np.all(np.diff(S) <= 0.0)
+    Sl = np.linalg.svd(X, compute_uv=False)
+    assert np.max(np.abs(S - Sl) / Sl) < 1e-12
+    assert np.abs(V.T @ V - np.eye(n)).max() < 64 * n * U64
+    assert np.abs(X @ V - Xi).max() < 1e-13
+
+
+def test_derijk_pivoting_on_a_permuted_diagonal():
+    """Orthogonal columns of distinct norms: no rotation, one sweep, and the columns come out
+    in descending norm order (perm = the order of decreasing norms)."""
+    d = np.array([0.5, 3.0, 1e-3, 2.0, 7.0])
+    X = np.zeros((7, 5))
+    X[[4, 0, 6, 2, 1], np.arange(5)] = d
+    Xi, V, perm, sw, rot, rc = oracle.jacobi_derijk(X, np.eye(5))
+    assert rc == 0 and rot == 0 and sw == 1
+    assert perm.tolist() == list(np.argsort(-d))
+    assert np.array_equal(np.linalg.norm(Xi, axis=0), np.sort(d)[::-1])
+
+
+@pytest.mark.parametrize("seed", [16, 17, 18])
+def test_derijk_pivoting_accelerates_convergence(seed):
+    """The paper's remark that de Rijk's pivoting accelerates Alg. 1, on seeded graded inputs
+    (sigma over 6 decades, columns scaled over 4 decades): no more sweeps than the cyclic order,
+    the same singular values."""
+    rng = np.random.default_rng(seed)
+    n = 40
+    X = inputs.known_sigma(rng, 50, n, np.logspace(0, -6, n)) * 10.0 ** rng.uniform(-4, 0, n)
+    _, _, sw_c, rot_c, rc_c = oracle.jacobi(X)
+    Xd, _, _, sw_d, rot_d, rc_d = oracle.jacobi_derijk(X)
+    assert rc_c == 0 and rc_d == 0
+    assert sw_d <= sw_c, (sw_d, sw_c)
+    Xc, _, _, _, _ = oracle.jacobi(X)
+    Sc = np.sort(np.linalg.norm(Xc, axis=0))[::-1]
+    assert np.max(np.abs(np.linalg.norm(Xd, axis=0) - Sc) / Sc) < 1e-10
+
+
 def _max_cos(X):
     Xn = X / np.linalg.norm(X, axis=0)
     G = np.abs(Xn.T @ Xn)
