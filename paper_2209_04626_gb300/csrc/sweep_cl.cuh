@@ -6,12 +6,18 @@
 // stores each column of Y and V, and the FP64 work of a visit (one pair) is separated by the
 // latencies of the loads and of the reduction and rotation-parameter chain. Here CTA r of a
 // cluster holds rows [r rpc, (r + 1) rpc) of the 2W columns (rpc = ceil(mX / CS)), so W = 4
-// fits at 8192 rows with CS = 4 and each CTA runs exactly the work of the W = 4 visit on a
-// 2048-row matrix. Per inner round, each CTA reduces its partial dot products, writes them
-// into every CTA's shared memory (distributed shared memory) and passes one cluster barrier;
-// then every CTA sums the CS partials in rank order and computes the same rotations (the same
-// bits: same operands, same order), so all CTAs of a cluster take the same decisions without
-// further exchange. V's rows are split over the cluster the same way.
+// fits at 8192 rows (CS = 8: 1024 rows and 128 threads per CTA, two CTAs of different visits
+// per SM) and each CTA runs the work of the W = 4 visit on a 1024-row matrix. Per inner round,
+// each CTA reduces its partial dot products, writes them into every CTA's shared memory
+// (distributed shared memory) and passes one cluster barrier; then every CTA sums the CS
+// partials in rank order and computes the same rotations (the same bits: same operands, same
+// order), so all CTAs of a cluster take the same decisions without further exchange. V's rows
+// are split over the cluster the same way.
+//
+// Late sweeps. Once a sweep's largest rotated cosine is below kClBatchCos, the next sweep's
+// rotations are of the order of its square and almost no visit rotates: each visit then
+// computes the dot products of all its pairs at once and passes a single cluster exchange
+// (cl_batch_quiet); only a visit with a pair to rotate runs the inner rounds.
 //
 // Uniform control flow. A cluster barrier waits for every CTA of the cluster, without a time
 // limit, so no CTA may leave while another waits at one. Every decision that reads state other
