@@ -58,6 +58,8 @@ def parse(argv=None):
     p.add_argument("--no-extras", action="store_true",
                    help="skip the plain/auto comparison, the 2048 x 1024 extra and the batch")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--batch-only", action="store_true",
+                   help="time only the uneven batch (--batch-count matrices), one JSON line")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     p.add_argument("--low-kernel", default="auto", choices=["auto", "tc", "reg"],
                    help="kernel of the binary32 stage (auto: by size)")
@@ -376,6 +378,50 @@ def tensor_flops_low(m, n, sweeps):
     return visits * 2 * 3 * 2.0 * m * 128 * 128
 
 
+def measure_batched(args, dev, stream, flush):
+    """The uneven batch (args.batch_count matrices) in one persistent launch: SVDs/s over three
+    timed calls after a tuning call, and an upper-bound roofline of its binary64 work."""
+    import torch
+    from paper_2209_04626_gb300 import inputs, mpjsvd
+    mats, _, bm, bn, bk = inputs.batch_matrices(count=args.batch_count)
+    dmats = [mpjsvd.colmajor(torch.from_numpy(X), dev) for X in mats]
+    hb = mpjsvd.Handle(mode="mixed")
+    hb.svd_batched(dmats)
+    torch.cuda.synchronize()
+    binfo = [None]
+
+    def bstep():
+        binfo[0] = hb.svd_batched(dmats)[3]
+    bms = time_calls(bstep, 3, stream, flush)
+    # roofline of the batched launch (binary64 work by the hot-path table's counts, with three
+    # refinement sweeps in which every pair rotates: an upper bound of the work done)
+    fl_b = sum(flops_svd_fp64(int(mi), int(ni), 3, 3 * int(ni) * (int(ni) - 1) // 2)
+               for mi, ni in zip(bm, bn))
+    ach_b = fl_b / (statistics.mean(bms) / 1000.0) / 1e12
+    out = {"workload": BATCH_WORKLOAD, "count": len(mats),
+           "svds_per_s": len(mats) / (statistics.mean(bms) / 1000.0),
+           "ms": statistics.mean(bms),
+           "nonzero_info": int((binfo[0] != 0).sum().item()),
+           "tuning": mpjsvd.mpjsvd_get_batched_tuning(hb.h),
+           "roofline": {"bound": "alu", "achieved_upper": ach_b, "peak": FP64_PEAK_DERIVED,
+                        "unit": "TFLOP/s", "frac_upper": ach_b / FP64_PEAK_DERIVED,
+                        "flop_model": "per matrix: RRQR 2mn^2 - 2n^3/3, switch 14n^3/3, "
+                                      "3 sweeps x n(n-1)/2 x 14n, U 4mn^2 - 2n^3 (upper bound)"}}
+    hb.close()
+    return out
+
+
+def batch_only(args):
+    """--batch-only: just the uneven batch (profiling and quick checks), one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = measure_batched(args, dev, torch.cuda.current_stream(dev), flush)
+    print(json.dumps({"batched": out}))
+    return 0
+
+
 def ours(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -516,112 +562,8 @@ def ours(args):
         extras["precision_2048x1024"] = pr
         del P, Uq, Sq, Vq
     if not args.no_extras:
-        mats, _, bm, bn, bk = inputs.batch_matrices(count=args.batch_count)
-        dmats = [mpjsvd.colmajor(torch.from_numpy(X), dev) for X in mats]
-        hb = mpjsvd.Handle(mode="mixed")
-        hb.svd_batched(dmats)
-        torch.cuda.synchronize()
-        binfo = [None]
+        extras["batched"] = measure_batched(args, dev, stream, flush)
 
-        def bstep():
-            binfo[0] = hb.svd_batched(dmats)[3]
-        bms = time_calls(bstep, 3, stream, flush)
-        # roofline of the batched launch (binary64 work by the hot-path table's counts, with three
-        # refinement sweeps in which every pair rotates: an upper bound of the work done)
-        fl_b = sum(flops_svd_fp64(int(mi), int(ni), 3, 3 * int(ni) * (int(ni) - 1) // 2)
-                   for mi, ni in zip(bm, bn))
-        ach_b = fl_b / (statistics.mean(bms) / 1000.0) / 1e12
-        extras["batched"] = {"workload": BATCH_WORKLOAD, "count": len(mats),
-                             "svds_per_s": len(mats) / (statistics.mean(bms) / 1000.0),
-                             "ms": statistics.mean(bms),
-                             "nonzero_info": int((binfo[0] != 0).sum().item()),
-                             "tuning": mpjsvd.mpjsvd_get_batched_tuning(hb.h),
-                             "roofline": {"bound": "alu", "achieved_upper": ach_b, "peak": FP64_PEAK_DERIVED,
-                                          "unit": "TFLOP/s", "frac_upper": ach_b / FP64_PEAK_DERIVED,
-                                          "flop_model": "per matrix: RRQR 2mn^2 - 2n^3/3, switch 14n^3/3, "
-                                                        "3 sweeps x n(n-1)/2 x 14n, U 4mn^2 - 2n^3 (upper bound)"}}
-        hb.close()
-        del dmats
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            dt, info = oracle_step(A_np)
-            cpu = {"value": 1.0 / dt, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
-                   "sample": info["sample"], "extrapolated": info["extrapolated"]}
-            if info["extrapolated"]:
-                cpu["parts_s"] = info["parts_s"]
-        except Exception as ex:  # reported, not fatal
-            cpu = {"value": None, "unit": "SVDs/s", "cores": 1, "kind": "oracle",
-                   "sample": "failed: %s" % ex}
-
-    if rank == 0:
-        line = {
-            "metric": "SVDs/s", "value": value, "unit": "SVDs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "m": m, "n": n, "mode": "mixed",
-                       "parallelism": "replicas",
-                       "l2": "flushed (256 MiB write) before each step; inputs %d MiB" % (m * n * 8 >> 20),
-                       "block_w_low": st["block_w_low"], "block_w_work": st["block_w_work"],
-                       "work_cluster": wcl,
-                       "qrcp": "mixed (Alg. 5)" if st["qrcp"] == 0 else "binary64"},
-            "roofline": {"kernel": ("k_sweeps_cl<double> (binary64 refinement sweeps, every visit split by "
-                                    "rows over a %d-CTA cluster, block width %d)" % (wcl, st["block_w_work"])
-                                    if wcl > 1 else
-                                    "k_sweeps<double> (binary64 refinement sweeps, one CTA per visit, block "
-                                    "width %d)" % st["block_w_work"]),
-                         "bound": "alu",
-                         "achieved": achieved, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_DERIVED, "traffic": traffic,
-                         "traffic_source": traffic_how,
-                         "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (the "
-                                         "SIMT DGEMM of the switch reaches 0.98 of it in the launch list)"),
-                         "peak_measured": fp64_measured,
-                         "peak_measured_source": ("mpjsvd_measure_fp64_peak in this run, after the timed "
-                                                  "region: independent FP64 FMA chains on every SM"),
-                         "flops_per_launch": fl_work, "ms_per_launch": avg_work_ms,
-                         "flop_model": "2n per pair per sweep + 12n per rotation (6n on Y, 6n on V)"},
-            "roofline_low": {"kernel": ("k_bsweeps_tf32 (binary32 stage, tensor cores)" if st["block_w_low"] == 64
-                                        else "k_sweeps<float> (binary32 stage)"), "bound": "alu",
-                             "achieved": fl_low / (avg_low_ms / 1000.0) / 1e12 if avg_low_ms > 0 else None,
-                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
-                             "flops_per_launch": fl_low, "ms_per_launch": avg_low_ms,
-                             "flop_model": "2n per pair per sweep + 6n per rotation (no V)",
-                         "low_kernel": ("tcgen05 TF32x3 blocked (64-column blocks)" if st["block_w_low"] == 64
-                                        else "register-resident level-1 visits")},
-            "phases_ms": phases,
-            "sweeps": {"low": st["sweeps_low"], "work": st["sweeps_work"],
-                       "rot_low": st["rot_low"], "rot_work": st["rot_work"],
-                       "rot_per_sweep_low": st["rot_sweep_low"][:min(16, st["sweeps_low"])],
-                       "rot_per_sweep_work": st["rot_sweep_work"][:min(16, st["sweeps_work"])],
-                       "max_cos_per_sweep_work": st["cos_sweep_work"][:min(16, st["sweeps_work"])]},
-            "fp64_gflops_whole_svd": flops_svd_fp64(m, n, st["sweeps_work"], st["rot_work"]) /
-            (total_ms / args.steps) / 1e6,
-            "compare": compare,
-            "accuracy": {"backward_fro": bw, "orth_U_max": orthU, "orth_V_max": orthV,
-                         "bound_orth": 64 * n * 2.0 ** -53, "status": st["status"]},
-            "e2e": {"value": e2e_value, "unit": "SVDs/s", "h2d_bytes_per_step": m * n * 8,
-                    "d2h_bytes_per_step": (m * n + n + n * n) * 8},
-            "gpu_launches": int(sum(s["launches"] for s in per_step_stats)),
-            "cpu_baseline": cpu,
-            "extras": extras,
-            "clocks": clk,
-            "wall_s": wall,
-        }
-        line["roofline_low"]["frac"] = (line["roofline_low"]["achieved"] / FP32_PEAK_TFLOPS
-                                        if line["roofline_low"]["achieved"] else None)
-        if st["block_w_low"] == 64 and avg_low_ms > 0:
-            tfl = tensor_flops_low(n, n, st["sweeps_low"])
-            line["roofline_low"]["tensor"] = {
-                "achieved_upper": tfl / (avg_low_ms / 1000.0) / 1e12, "peak": TF32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac_upper": tfl / (avg_low_ms / 1000.0) / 1e12 / TF32_PEAK_TFLOPS,
-                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x 1.1 / 2.25 (nominal tf32 : bf16)",
-                "flop_model": "per visit 2 x 3 x 2 m 128^2 (Gram and application, three TF32 products "
-                              "each), every visit counted as rotating"}
-        print(json.dumps(line))
     h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -632,6 +574,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.batch_only:
+        return batch_only(args)
     return ours(args)
 
 
