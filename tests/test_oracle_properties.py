@@ -37,3 +37,37 @@ def test_oracle_options_give_the_svd(seed, n, extra, mode, precond, switch_metho
     for k in range(n):  # sign rule: the largest-magnitude entry of v_k is positive
         r = int(np.argmax(np.abs(V[:, k])))
         assert V[r, k] >= 0.0
+
+
+def test_block_reflector_ut_form_matches_the_product_of_householder_reflectors():
+    """The compact form the two-level QR applies (Joffrain, Low, Quintana-Orti, van de Geijn):
+    for reflectors H_j = I - tau_j v_j v_j^T (the oracle's Householder QR, geqrf layout, one
+    zero reflector included), Q = H_1 ... H_k = I - V T V^T with T^{-1} = S = striu(V^T V) +
+    diag(1 / tau). Checked against the oracle's own application of the reflectors: Q^T C =
+    C - V X with S^T X = V^T C by forward substitution, Q C = C - V X with S X = V^T C by back
+    substitution, each x_i multiplied by tau_i (so tau = 0 contributes nothing)."""
+    rng = np.random.default_rng(71)
+    m, k = 40, 12
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-6, 0, k)
+    A[:, 5] = 0.0  # stays zero under the earlier reflectors: its own reflector has tau = 0
+    QR, tau = oracle.geqrf(A)
+    assert tau[5] == 0.0 and np.all(tau[np.arange(k) != 5] != 0.0)
+    V = np.tril(QR[:, :k], -1) + np.eye(m, k)
+    G = V.T @ V
+    C = rng.standard_normal((m, 7))
+
+    def subst(W, upper):
+        X = W.copy()
+        order = range(k - 1, -1, -1) if upper else range(k)
+        for i in order:
+            if upper:
+                acc = X[i] - G[i, i + 1:] @ X[i + 1:]
+            else:
+                acc = X[i] - G[:i, i] @ X[:i]
+            X[i] = acc * tau[i]
+        return X
+
+    QtC = C - V @ subst(V.T @ C, upper=False)
+    QC = C - V @ subst(V.T @ C, upper=True)
+    assert np.abs(QtC - oracle.apply_q(QR, tau, C, trans=True)).max() < 1e-13
+    assert np.abs(QC - oracle.apply_q(QR, tau, C, trans=False)).max() < 1e-13
