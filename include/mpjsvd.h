@@ -18,7 +18,11 @@
  *      rotations were all negligible, as the paper's experiments run Alg. 1);
  *   6. Sigma = column norms, U_X = normalized columns, sorted descending; U and V are
  *      assembled from the factors (Alg. 4, last line).
- * Every stage runs as hand-written CUDA kernels on the handle's stream.
+ * Every stage runs as hand-written CUDA kernels on the handle's stream. For large n the
+ * binary64 sweeps split each visit of a block pair by rows over a thread-block cluster
+ * (params.work_kernel), and the blocked QRs apply their reflectors in 256-column blocks
+ * whose binary64 products run on the bf16 tensor cores by error-free splitting
+ * (params.qr_update); both compute the same method.
  *
  * Departures from the plain statement of the method, each with the same limit:
  *   - the binary64 stage evaluates each rotation's tangent in binary32 from the binary64
