@@ -72,6 +72,10 @@ def test_default_params_are_the_papers(lib_path):
     assert (p.tol_alg, p.tol_orth, p.tol_cond_coef) == (1e-2, 1e-5, 1.5)
     assert p.trailing_frac == 0.25 and p.maxsweep == 30 and p.block_w == 0
     assert p.mode == 0 and p.precond == 0 and p.qr_first == 0 and p.qrcp == 0 and p.stop == 0
+    # the kernel choices default to the automatic ones (by size), the options of Section 3.4 off
+    assert p.wait_limit_ms == 4000 and p.low_kernel == 0 and p.gemm_kernel == 0
+    assert p.work_kernel == 0 and p.work_cluster == 0 and p.qr_update == 0
+    assert p.v_by_qr == 0 and p.switch_method == 0 and p.y_tol == 0.0
 
 
 def test_argument_validation_without_gpu(lib_path):
