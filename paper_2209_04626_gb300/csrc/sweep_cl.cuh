@@ -572,6 +572,34 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
             const unsigned R = (unsigned)(sweep * rounds + r);
             if (!cl_agree<W, CS>(cl, sm, par, rank, cl_wait_local(D.ver, bi, bj, R, st), 0, nullptr)) return;
             const int nrot = cl_visit_x<W, RPT, CS>(cl, D, X, bi, bj, r == 0, sm, par, rank, xr, batch);
+            if (nrot == 0) {
+                // (the same in every CTA) nothing of X or V was stored but rank 0's norms, and every
+                // rank read its rows before the visit's last exchange: rank 0 alone passes the
+                // blocks on (X now; V once the previous round's replays on them are done). A wait
+                // that gives up records the failure, which the sweep's grid barrier reports to all.
+                if (rank == 0 && tid == 0) {
+                    __threadfence();
+                    st_release_u32(D.ver + bi, R + 1);
+                    st_release_u32(D.ver + bj, R + 1);
+                    if (WITH_V) {
+                        const uint64_t t0 = globaltimer_ns(), lim = spin_limit_ns(st);
+                        bool ok = true;
+                        unsigned spins = 0;
+                        while (ld_acquire_u32(vv + bi) < R || ld_acquire_u32(vv + bj) < R) {
+                            if ((++spins & 255u) == 0 && (call_failed(st) || globaltimer_ns() - t0 > lim)) {
+                                if (!call_failed(st)) atomicOr(&st->status, MPJSVD_STATUS_TIMEOUT);
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (ok) {
+                            st_release_u32(vv + bi, R + 1);
+                            st_release_u32(vv + bj, R + 1);
+                        }
+                    }
+                }
+                continue;
+            }
             if (tid == 0) __threadfence();  // this CTA's stores before the barrier below
             // V's versions (each CTA acquires them for itself) and the release of X: after this
             // barrier every rank's X stores precede rank 0's release
