@@ -3,9 +3,10 @@ large-workload recipe (single matrix, the launch configurations of the bench: 25
 dataflow sweeps, the binary32 stage at 128 blocks) against the binary64 oracle element by
 element, and the 4096-matrix uneven batch (one persistent launch) by the factorization bars on
 every matrix plus the oracle on a seeded sample that spans every size decile. The 8192 x 8192
-large workload itself is beyond the oracle's reach in a test (hours single-threaded); its
-recipe at n = 1024 runs the same code path with the same block widths per sweep stage, and
-the full size is checked by properties that hold at any size."""
+large workload itself is beyond the oracle's reach in a test (hours single-threaded): its
+recipe at n = 1024 is checked against the oracle element by element, and the full size, in the
+bench's own launch configuration, by properties that hold at any size (the factorization bars,
+the plain binary64 pipeline's singular values, residuals of sampled singular triplets)."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,47 @@ def test_batched_4096_full():
         _, So, _, _ = oracle.svd(A, mode="mixed", qrcp=1)
         sigma_gate(A, S, So)
     h.close()
+
+
+def test_large_8192_full_size_properties():
+    """The bench's headline matrix at its full size and in the bench's launch configuration
+    (8-CTA cluster-split refinement, tensor-core binary32 stage, two-level QRs), beyond the
+    oracle's reach in a test: the factorization bars on the GPU in binary64; singular values
+    sorted and equal to the plain binary64 pipeline's to 1e-12 relative (kappa(B) = 1e2); and
+    for every 512th singular triplet the residuals A v - s u, A^T u - s v and the Rayleigh
+    quotient u^T A v computed on the host in binary64."""
+    import torch
+    from paper_2209_04626_gb300 import mpjsvd
+    n = 8192
+    A_np = inputs.large_8192()
+    dev = torch.device("cuda")
+    A = mpjsvd.colmajor(torch.from_numpy(A_np), dev)
+    h = mpjsvd.Handle(mode="mixed")
+    U, S, V = h.svd(A)
+    st = h.stats()
+    h.close()
+    assert st["status"] == 0, st
+    assert st["work_cluster"] == 8 and st["block_w_work"] == 4 and st["block_w_low"] == 64, st
+    U64 = 2.0 ** -53
+    with torch.no_grad():
+        bw = float(torch.linalg.norm(A - (U * S) @ V.t()) / torch.linalg.norm(A))
+        eye = torch.eye(n, dtype=torch.float64, device=dev)
+        orth_u = float((U.t() @ U - eye).abs().max())
+        orth_v = float((V.t() @ V - eye).abs().max())
+        del eye
+    assert bw <= 1e-13 and orth_u <= 64 * n * U64 and orth_v <= 64 * n * U64, (bw, orth_u, orth_v)
+    Sh = S.cpu().numpy()
+    assert np.all(np.diff(Sh) <= 0.0) and Sh[-1] > 0.0
+    hp = mpjsvd.Handle(mode="plain")
+    _, Sp, _ = hp.svd(A)
+    hp.close()
+    Sp = Sp.cpu().numpy()
+    assert np.max(np.abs(Sh - Sp) / Sp) <= 1e-12
+    idx = np.arange(0, n, 512)
+    Uh, Vh = U[:, idx].cpu().numpy(), V[:, idx].cpu().numpy()
+    nA = np.linalg.norm(A_np)
+    for j, i in enumerate(idx):
+        r1 = A_np @ Vh[:, j] - Sh[i] * Uh[:, j]
+        r2 = A_np.T @ Uh[:, j] - Sh[i] * Vh[:, j]
+        assert np.linalg.norm(r1) <= 1e-13 * nA and np.linalg.norm(r2) <= 1e-13 * nA, i
+        assert abs(Uh[:, j] @ (A_np @ Vh[:, j]) - Sh[i]) <= 1e-13 * nA, i
