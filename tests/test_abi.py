@@ -87,3 +87,27 @@ def test_argument_validation_without_gpu(lib_path):
     assert f(None, 4, 2, None, 4, None, None, None, 0.0) == -1
     lib.mpjsvd_default_params.argtypes = [ctypes.c_void_p]
     assert lib.mpjsvd_default_params(None) == -1
+
+
+def test_python_choice_names_match_the_header_constants(lib_path):
+    """Every name the binding accepts for an algorithm choice maps to the value of the header's
+    #define of the same choice (MPJSVD_<GROUP>_<NAME>), and every such #define has a name."""
+    import re
+    from paper_2209_04626_gb300 import mpjsvd
+    hdr = open(os.path.join(ROOT, "include", "mpjsvd.h")).read()
+    groups = {"MODE": mpjsvd.MODE, "PRECOND": mpjsvd.PRECOND, "QRCP": mpjsvd.QRCP, "STOP": mpjsvd.STOP,
+              "LOWK": mpjsvd.LOWK, "SWITCH": mpjsvd.SWITCH, "GEMMK": mpjsvd.GEMMK, "WORKK": mpjsvd.WORKK,
+              "QRU": mpjsvd.QRU}
+    aliases = {"RT": "rt", "ALG1": "alg1", "XGESVJ": "xgesvj", "REG": "reg", "CTA": "cta"}
+    for g, names in groups.items():
+        defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define MPJSVD_%s_(\w+) (\d+)" % g, hdr)}
+        assert defs, g
+        assert sorted(defs.values()) == sorted(names.values()), (g, defs, names)
+        for cname, val in defs.items():
+            key = aliases.get(cname, cname.lower())
+            assert names.get(key) == val, (g, cname, key, names)
+        # and the binding maps them into the params struct
+        field = {"MODE": "mode", "PRECOND": "precond", "QRCP": "qrcp", "STOP": "stop", "LOWK": "low_kernel",
+                 "SWITCH": "switch_method", "GEMMK": "gemm_kernel", "WORKK": "work_kernel", "QRU": "qr_update"}[g]
+        for key, val in names.items():
+            assert getattr(mpjsvd.mpjsvd_default_params(**{field: key}), field) == val
